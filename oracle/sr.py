@@ -1,0 +1,83 @@
+"""VMC estimators and the modified natural-gradient update (Sec. III).
+
+With samples s drawn from |psi_s|^2 / <psi|psi> (or, in enumeration mode,
+exact weights p_s = |psi_s|^2 / sum |psi|^2 over the whole S^z sector):
+
+    S_kk' = <O_k* O_k'> - <O_k>* <O_k'>
+    gamma = arccos sqrt( |<R>|^2 / <|R|^2> )
+    F_k   = dgamma * gamma cot(gamma) * ( <O_k* R> / <R> - <O_k*> )
+
+and the update solves sum_k' (S + lambda I)_kk' dalpha_k' = F_k, then sets
+alpha <- alpha + dalpha.  Readings of points the paper leaves open:
+  * the diagonal shift is additive, S + lambda I;
+  * the argument of the arccos is clamped to <= 1 (sampling noise can push
+    it above), and gamma cot gamma is taken as 1 when gamma < 1e-8;
+  * the shifted system is solved by Cholesky (S + lambda I is Hermitian
+    positive definite for lambda > 0).
+"""
+
+import numpy as np
+import scipy.linalg
+
+
+def _mean(x, weights):
+    if weights is None:
+        return np.mean(x, axis=0)
+    return np.tensordot(weights, x, axes=(0, 0))
+
+
+def estimators(O, R, weights=None):
+    """The sample averages the update needs.
+
+    O [B, P] complex log-derivatives, R [B] complex ratios, weights [B] (sum 1)
+    or None for plain sample means.
+    """
+    O = np.asarray(O, dtype=np.complex128)
+    R = np.asarray(R, dtype=np.complex128)
+    return {
+        "mR": _mean(R, weights),
+        "mRR": _mean(np.abs(R) ** 2, weights).real,
+        "Obar": _mean(O, weights),
+        "OR": _mean(np.conj(O) * R[:, None], weights),
+        "OO": (np.conj(O).T * (np.ones(len(R)) / len(R) if weights is None else weights)) @ O,
+    }
+
+
+def fubini_study_angle(mR, mRR):
+    """gamma = arccos sqrt(|<R>|^2 / <|R|^2>), argument clamped to <= 1."""
+    return float(np.arccos(np.sqrt(min(1.0, abs(mR) ** 2 / mRR))))
+
+
+def gamma_cot_gamma(gamma):
+    return 1.0 if gamma < 1e-8 else gamma / np.tan(gamma)
+
+
+def force(est, dgamma):
+    """F_k and gamma from the estimators."""
+    gamma = fubini_study_angle(est["mR"], est["mRR"])
+    c = dgamma * gamma_cot_gamma(gamma)
+    F = c * (est["OR"] / est["mR"] - np.conj(est["Obar"]))
+    return F, gamma
+
+
+def qgt(est):
+    """S = <O* O^T> - <O>* <O>^T  (the quantum geometric tensor, Sec. III)."""
+    return est["OO"] - np.outer(np.conj(est["Obar"]), est["Obar"])
+
+
+def shifted_solve(S, F, shift):
+    """Solve (S + shift I) x = F by Cholesky."""
+    A = S + shift * np.eye(S.shape[0])
+    c = scipy.linalg.cho_factor(A, lower=True)
+    return scipy.linalg.cho_solve(c, F)
+
+
+def sr_step(params, O, R, shift, dgamma, weights=None):
+    """One natural-gradient update.  Returns (new params, info dict)."""
+    est = estimators(O, R, weights)
+    F, gamma = force(est, dgamma)
+    S = qgt(est)
+    delta = shifted_solve(S, F, shift)
+    info = {"gamma": gamma, "mR": est["mR"], "mRR": est["mRR"], "F": F, "S": S,
+            "delta": delta, "Obar": est["Obar"], "OR": est["OR"]}
+    return np.asarray(params, dtype=np.complex128) + delta, info

@@ -1,0 +1,89 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the tests.
+
+Holds none of the method's arithmetic: only random draws and workload
+shapes.  The paper's own inputs (trained ground-state RBMs of an L = 32
+chain and a 6 x 6 square lattice) are not available, so random complex RBMs
+of the same architecture stand in for them.
+
+  * RBM parameters: Re and Im of every entry of [a | b | W] i.i.d.
+    N(0, sigma^2), drawn from numpy's Philox bit generator with the given
+    seed (Re block first, then Im block).
+  * Walker configurations: each row an independent uniform random
+    permutation of N/2 up and N/2 down spins (the S^z = 0 sector).
+"""
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def rbm_params(seed, N, M, sigma):
+    """complex128 [N + M + N*M]."""
+    g = np.random.Generator(np.random.Philox(seed))
+    P = N + M + N * M
+    re = g.standard_normal(P)
+    im = g.standard_normal(P)
+    return sigma * re + 1j * sigma * im
+
+
+def sz0_spins(seed, B, N):
+    """int8 [B, N], each row a random S^z = 0 configuration."""
+    if N % 2:
+        raise ValueError("the S^z = 0 sector needs an even number of sites")
+    g = np.random.Generator(np.random.Philox(seed))
+    base = np.tile(np.array([1] * (N // 2) + [-1] * (N // 2), dtype=np.int8), (B, 1))
+    return g.permuted(base, axis=1)
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    Lx: int
+    Ly: int
+    alpha: int          # M = alpha * N
+    sigma: float        # weight scale of the random RBM
+    q: tuple            # probe momentum (qx, qy)
+    walkers: int
+    moments: int
+    iters: int          # natural-gradient iterations per moment
+    shift: float = 1e-3
+    dgamma: float = 0.5
+
+    @property
+    def N(self):
+        return self.Lx * self.Ly
+
+    @property
+    def M(self):
+        return self.alpha * self.N
+
+    @property
+    def P(self):
+        return self.N + self.M + self.N * self.M
+
+    @property
+    def n_bonds(self):
+        return self.N if self.Ly == 1 else 2 * self.N
+
+
+# The workload shapes.  Where the paper reports a system (L = 32 chain,
+# 100 moments; 6 x 6 square lattice) these synthetic lattices stand in.
+WORKLOADS = {
+    "chain12_fp64": Workload("chain12_fp64", 12, 1, 1, 0.05, (np.pi, 0.0), 1024, 10, 20),
+    "chain64": Workload("chain64", 64, 1, 2, 0.02, (np.pi / 2, 0.0), 16384, 100, 50),
+    "square10": Workload("square10", 10, 10, 1, 0.01, (np.pi, np.pi), 32768, 200, 50),
+    "square8": Workload("square8", 8, 8, 2, 0.02, (np.pi, np.pi), 8192, 150, 50),
+    "chain48": Workload("chain48", 48, 1, 2, 0.02, (np.pi / 2, 0.0), 8192, 150, 50),
+    "chain96": Workload("chain96", 96, 1, 2, 0.02, (np.pi / 2, 0.0), 8192, 150, 50),
+    "square16": Workload("square16", 16, 16, 1, 0.01, (np.pi, 0.0), 65536, 300, 50),
+}
+
+
+def safe_rescaling(Lx, Ly, J=1.0, Wp=0.9875):
+    """(E0, a) from the rigorous spectrum bounds -3/4 J N_b <= H <= J N_b / 4.
+
+    With these, H' = (H - E0)/a - W' maps the whole spectrum into [-W', W'],
+    whatever the probed state; used where no exact ground energy is known."""
+    nb = Lx * Ly if Ly == 1 else 2 * Lx * Ly
+    lo, hi = -0.75 * J * nb, 0.25 * J * nb
+    return lo, (hi - lo) / (2 * Wp)

@@ -1,0 +1,160 @@
+"""Pins for the oracle's natural-gradient estimators and its Chebyshev driver.
+
+The VMC forms (sample averages of O_k and R) are checked against the
+bra-ket forms of the same quantities, built from dense vectors and
+finite-difference parameter derivatives; the driver's beta_n and mu_n are
+checked against dense inner products."""
+
+import numpy as np
+import pytest
+
+from oracle import chebyshev, exact, rbm, sr
+
+
+def _dense_psi(p, N, M, basis):
+    return exact.rbm_vector(p, N, M, basis)
+
+
+def test_vmc_estimators_equal_braket_forms():
+    N, M = 6, 4
+    basis = exact.sector_basis(N)
+    rng = np.random.default_rng(10)
+    p = rbm.init_params(rng, N, M, 0.4)
+    psi = _dense_psi(p, N, M, basis)
+    phi = psi * (1 + 0.3 * rng.standard_normal(len(basis))) + 0.2 * rng.standard_normal(len(basis))
+    Z = np.vdot(psi, psi).real
+    # finite-difference derivative vectors d psi / d alpha_k (holomorphic, real step)
+    P = rbm.n_params(N, M)
+    h = 1e-6
+    dpsi = np.empty((P, len(basis)), dtype=np.complex128)
+    for k in range(P):
+        e = np.zeros(P, dtype=np.complex128)
+        e[k] = h
+        dpsi[k] = (_dense_psi(p + e, N, M, basis) - _dense_psi(p - e, N, M, basis)) / (2 * h)
+    dgamma = 0.37
+    gamma_d = np.arccos(abs(np.vdot(psi, phi)) / np.sqrt(Z * np.vdot(phi, phi).real))
+    c = dgamma * gamma_d / np.tan(gamma_d)
+    dpsi_vec = c * ((Z / np.vdot(psi, phi)) * phi - psi)
+    # rotation properties of the update direction
+    assert abs(np.vdot(psi, dpsi_vec)) < 1e-12 * Z
+    assert np.vdot(dpsi_vec, dpsi_vec).real == pytest.approx((dgamma * gamma_d) ** 2 * Z, rel=1e-10)
+    S_bk = (np.conj(dpsi) @ dpsi.T) / Z - np.outer(np.conj(dpsi) @ psi, np.conj(psi) @ dpsi.T) / Z ** 2
+    F_bk = (np.conj(dpsi) @ dpsi_vec) / Z - (np.conj(dpsi) @ psi) / Z * np.vdot(psi, dpsi_vec) / Z
+    # VMC forms in enumeration mode
+    w = np.abs(psi) ** 2 / Z
+    O = rbm.logderiv(p, N, M, basis)
+    est = sr.estimators(O, phi / psi, weights=w)
+    F, gamma = sr.force(est, dgamma)
+    S = sr.qgt(est)
+    assert gamma == pytest.approx(gamma_d, rel=1e-12)
+    assert np.allclose(S, S_bk, atol=1e-7)
+    assert np.allclose(F, F_bk, atol=1e-7)
+    assert np.allclose(S, S.conj().T, atol=1e-14)
+    assert np.linalg.eigvalsh(S).min() > -1e-12
+
+
+def test_exact_representability_gives_zero_angle_and_force():
+    N, M = 6, 4
+    basis = exact.sector_basis(N)
+    p = rbm.init_params(np.random.default_rng(11), N, M, 0.4)
+    c = 0.3 - 1.7j
+    O = rbm.logderiv(p, N, M, basis)
+    w = np.abs(_dense_psi(p, N, M, basis)) ** 2
+    est = sr.estimators(O, np.full(len(basis), c), weights=w / w.sum())
+    F, gamma = sr.force(est, 0.5)
+    assert gamma < 1e-7 and np.allclose(F, 0, atol=1e-12)
+    assert est["mR"] == pytest.approx(c)
+
+
+def test_shifted_solve_residual():
+    rng = np.random.default_rng(12)
+    O = rng.standard_normal((50, 20)) + 1j * rng.standard_normal((50, 20))
+    est = sr.estimators(O, rng.standard_normal(50) + 0j)
+    S = sr.qgt(est)
+    F = rng.standard_normal(20) + 1j * rng.standard_normal(20)
+    x = sr.shifted_solve(S, F, 1e-3)
+    assert np.linalg.norm((S + 1e-3 * np.eye(20)) @ x - F) < 1e-10 * np.linalg.norm(F)
+
+
+def test_natural_gradient_fit_converges_on_representable_target():
+    # phi = i sigma_0 psi0 is exactly the RBM psi0 with a_0 += i pi / 2.
+    N, M = 8, 8
+    basis = exact.sector_basis(N)
+    rng = np.random.default_rng(13)
+    p0 = rbm.init_params(rng, N, M, 0.3)
+    phi = 1j * basis[:, 0] * _dense_psi(p0, N, M, basis)
+    p = p0.copy()
+    p[0] += 0.5j * np.pi
+    p = p + 0.02 * (rng.standard_normal(len(p)) + 1j * rng.standard_normal(len(p)))
+    gammas = []
+    for _ in range(40):
+        psi = _dense_psi(p, N, M, basis)
+        w = np.abs(psi) ** 2
+        p, info = sr.sr_step(p, rbm.logderiv(p, N, M, basis), phi / psi, 1e-6, 0.5, weights=w / w.sum())
+        gammas.append(info["gamma"])
+    assert gammas[-1] < 1e-3 * gammas[0]
+
+
+def _cfg(**kw):
+    # E0 and a from the exact spectrum, so that H' maps it onto [-W', W']
+    e = np.linalg.eigvalsh(exact.hamiltonian(8, 1, 1.0, exact.sector_basis(8)))
+    base = dict(Lx=8, Ly=1, M=8, q=(np.pi / 2, 0.0), n_moments=4, n_iter=12, shift=1e-3,
+                dgamma=0.5, E0=e[0], a=(e[-1] - e[0]) / (2 * 0.9875), Wp=0.9875, n_therm=5,
+                sweeps_per_iter=1)
+    base.update(kw)
+    return chebyshev.Config(**base)
+
+
+def test_enumerated_driver_betas_and_moments_against_dense_vectors():
+    cfg = _cfg(M=16, n_iter=40)
+    N, M = cfg.N, cfg.M
+    basis = exact.sector_basis(N)
+    psi_p = rbm.init_params(np.random.default_rng(14), N, M, 0.2)
+    res = chebyshev.run_enumerated(cfg, psi_p)
+    H = exact.hamiltonian(cfg.Lx, cfg.Ly, cfg.J, basis)
+    Hp = exact.rescaled(H, cfg.E0, cfg.a, cfg.Wp)
+    psi = _dense_psi(psi_p, N, M, basis)
+    Z = np.vdot(psi, psi).real
+    t0 = exact.probe_vector(cfg.Lx, cfg.Ly, cfg.q[0], cfg.q[1], basis, psi)
+    assert res.mu[0] == pytest.approx(np.vdot(t0, t0).real / Z, rel=1e-12)
+    dense = [t0] + [_dense_psi(s.params, N, M, basis) for s in res.states[1:]]
+    for n in range(1, cfg.n_moments):
+        phi = res.betas[n - 1] * (Hp @ dense[n - 1]) if n == 1 else \
+            2 * res.betas[n - 1] * (Hp @ dense[n - 1]) - res.betas[n - 2] * dense[n - 2]
+        beta = np.vdot(dense[n], phi) / np.vdot(dense[n], dense[n])
+        assert res.betas[n] == pytest.approx(beta, rel=1e-10)
+        assert res.mu[n] == pytest.approx(res.betas[n] * np.vdot(t0, dense[n]) / Z, rel=1e-10)
+    # accuracy report, not a parity gate: with alpha = 2 the fits of t_1 and
+    # t_2 converge (gamma -> 1e-4) and their moments match the exact ones;
+    # t_3 stalls at a large angle from its warm start (force ~ cot gamma -> 0).
+    mu_ex = exact.chebyshev_moments(Hp, t0, psi, cfg.n_moments)
+    assert res.gammas[0][-1] < 1e-3 and res.gammas[1][-1] < 1e-2
+    for n in (1, 2):
+        assert abs(res.mu[n] - mu_ex[n]) < 0.01 * abs(mu_ex[0])
+
+
+def test_sampled_driver_tracks_enumeration_within_mc_error():
+    # 12-site chain, q = pi, alpha = 1, weights sigma = 0.05, paper rescaling
+    # (a = 5, E0 = exact ground energy): the shape of the FP64 chain workload.
+    basis = exact.sector_basis(12)
+    e0 = np.linalg.eigvalsh(exact.hamiltonian(12, 1, 1.0, basis))[0]
+    cfg = chebyshev.Config(Lx=12, Ly=1, M=12, q=(np.pi, 0.0), n_moments=3, n_iter=20,
+                           E0=e0, a=5.0, Wp=0.9875, n_therm=10, n_therm_ref=40)
+    N, M = cfg.N, cfg.M
+    psi_p = rbm.init_params(np.random.default_rng(0), N, M, 0.05)
+    rng = np.random.default_rng(1)
+    base = np.array([1] * (N // 2) + [-1] * (N // 2), dtype=np.int8)
+    s_fit = rng.permuted(np.tile(base, (1024, 1)), axis=1)
+    s_ref = rng.permuted(np.tile(base, (1024, 1)), axis=1)
+    res_s = chebyshev.run_sampled(cfg, psi_p, s_fit, s_ref)
+    res_e = chebyshev.run_enumerated(cfg, psi_p)
+    mu0 = abs(res_e.mu[0])
+    for n in range(cfg.n_moments):
+        assert abs(res_s.mu[n] - res_e.mu[n]) < 0.05 * mu0, n
+    assert np.all(res_s.spins_fit.sum(axis=1) == 0)
+    # and the enumerated moments sit close to the exact ones (fit error only)
+    Hp = exact.rescaled(exact.hamiltonian(12, 1, 1.0, basis), cfg.E0, cfg.a, cfg.Wp)
+    psi = exact.rbm_vector(psi_p, N, M, basis)
+    t0 = exact.probe_vector(12, 1, np.pi, 0.0, basis, psi)
+    mu_ex = exact.chebyshev_moments(Hp, t0, psi, cfg.n_moments)
+    assert np.max(np.abs(np.array(res_e.mu) - mu_ex)) < 0.01 * mu0
