@@ -1,0 +1,383 @@
+"""Throughput of the RBM-Chebyshev projection step on one GB300.
+
+One step = one Chebyshev moment n of the 64-site chain workload: fit RBM_n to
+phi_n = 2 beta_{n-1} H' t~_{n-1} - beta_{n-2} t~_{n-2} by 50 natural-gradient
+iterations over 16384 walkers (each iteration: one Metropolis sweep, the local
+target R, the reductions, the matrix-free shifted solve, theta refresh),
+then beta_n = <R> and mu_n with its Krylov columns.  Inputs are synthetic
+(random complex RBM, alpha = 2, sigma = 0.02, q = pi/2) and resident in HBM;
+L2 is flushed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun every rank runs an independent
+sequence (a different seed): weak scaling with no data-path collective.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "chain64"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed"])
+    ap.add_argument("--cg-maxit", type=int, default=50)
+    ap.add_argument("--cg-tol", type=float, default=1e-4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-walkers", type=int, default=2048)
+    return ap.parse_args()
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    def __init__(self, path, index):
+        self.path, self.index, self.p = path, index, None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            self.p.wait()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(np.max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except ValueError:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def make_config(wl, E0, a, args, n_moments, seed):
+    from paper_2103_08804_gb300 import api, driver
+    return driver.SeqConfig(Lx=wl.Lx, Ly=wl.Ly, M=wl.M, q=wl.q, n_moments=n_moments,
+                            n_iter=wl.iters, shift=wl.shift, dgamma=wl.dgamma, E0=E0, a=a,
+                            Wp=0.9875, n_therm=2, sweeps_per_iter=1, n_therm_ref=20, seed=seed,
+                            seed_ref=seed + 1, solver=api.SOLVE_CG, cg_maxit=args.cg_maxit,
+                            cg_tol=args.cg_tol, krylov=True)
+
+
+def reduce_flops(wl):
+    """Algorithmic flops of one launch of the O-reduction over all walkers:
+    per (walker, i, j) one real x complex FMA for O_W (4 flops), per (walker, j)
+    conj(T) g (6 flops) and its b-sum (2 flops), per (walker, i) 4 flops."""
+    B, N, M = wl.walkers, wl.N, wl.M
+    return B * (4 * N * M + 8 * M + 4 * N)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2103_08804_gb300 import api, driver, synth
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    wl = synth.WORKLOADS[WORKLOAD]
+    E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
+    K, W = args.steps, args.warmup
+    n_moments = 1 + W + 2 * K
+    seed = 1000 + 17 * rank
+    prec = api.FP32 if args.prec == "fp32" else api.MIXED
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(wl.Lx, wl.Ly, wl.M, wl.walkers, prec=prec, stream=stream)
+    psi = synth.rbm_params(seed, wl.N, wl.M, wl.sigma)
+    cfg = make_config(wl, E0, a, args, n_moments, seed)
+    seq = driver.Sequence(ctx, cfg, psi, synth.sz0_spins(seed + 2, wl.walkers, wl.N),
+                          synth.sz0_spins(seed + 3, wl.walkers, wl.N))
+    seq.start()
+    for n in range(1, 1 + W):
+        seq.fit(n)
+    ctx.sync_status()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    kernel = "reduce"
+    per_step_launches = None
+    ctx.time_kernel(kernel, 4096)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches0 = ctx.n_launches()
+    wall0 = time.perf_counter()
+    with ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")
+                      if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                      else f"/tmp/clocks_r{rank}.csv", local) as clk:
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            seq.fit(1 + W + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(ws)
+    launches = ctx.n_launches() - launches0
+    per_step_launches = launches / K
+    ktimes = ctx.kernel_times()
+    ctx.time_kernel(None, 1)
+    ctx.sync_status()
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    ms = max_over_ranks(ws, float(np.mean(step_ms)))
+    # stats of the timed moments
+    st = seq.stats[1 + W:1 + W + K].cpu().numpy()
+    cg_iters = float(st[..., 5].mean())
+    # ------------------------------------------------------------ end to end
+    e2e_ms, Bi, Bo = e2e(seq, ctx, 1 + W + K, K, stream)
+    e2e_ms = max_over_ranks(ws, e2e_ms)
+    peaks, peak_src = measured_peaks()
+    clocks = clk.summary()
+    f_sm = clocks.get("sm_mhz") or 2070.0
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_sm * 1e6 / 1e12
+    k_ms = float(np.mean(ktimes)) if ktimes else None
+    achieved = reduce_flops(wl) / (k_ms * 1e-3) / 1e12 if k_ms else None
+    sweeps_per_moment = cfg.n_therm + cfg.n_iter * cfg.sweeps_per_iter + cfg.sweeps_per_iter
+    value = ws * 3600.0 * 1000.0 / ms
+    out = {
+        "metric": "Chebyshev moments/hour",
+        "value": value,
+        "unit": "moments/hour",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (products), f64 (sums, CG)" if prec == api.FP32 else "mixed",
+        "data": "synthetic (random complex RBM, sigma=0.02; seeded S^z=0 walkers)",
+        "config": {"workload": "chain64: periodic Heisenberg chain N=64, RBM alpha=2 (M=128, "
+                               "P=8384), 16384 walkers, q=pi/2, 50 natural-gradient iterations "
+                               "per moment, matrix-free CG shifted solve",
+                   "path": "plain fp32" if prec == api.FP32 else "mixed",
+                   "walkers": wl.walkers, "iters_per_moment": wl.iters,
+                   "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol,
+                   "cg_iters_mean": cg_iters, "l2": "256 MiB buffer written between timed steps",
+                   "parallelism": f"replicas x{ws}"},
+        "mc_samples_per_s": ws * wl.walkers * sweeps_per_moment / (ms * 1e-3),
+        "mc_samples_unit": "walker-sweeps/s (one sweep = N exchange proposals)",
+        "gpu_launches": int(round(per_step_launches * K)),
+        "gpu_launches_per_step": per_step_launches,
+        "wall_s_timed": wall,
+        "clocks": clocks,
+        "e2e": {"value": ws * 3600.0 * 1000.0 / e2e_ms, "unit": "moments/hour",
+                "h2d_bytes_per_step": Bi, "d2h_bytes_per_step": Bo},
+        "roofline": {"kernel": "oreduce_kernel (sum_s op(O_k) g_s)", "bound": "alu",
+                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
+                     "launches_timed": len(ktimes), "avg_launch_ms": k_ms,
+                     "flops_per_launch": reduce_flops(wl),
+                     "peak_source": "FP32 lanes x 2 x median SM clock under load"},
+        "peaks_file": peak_src,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e(seq, ctx, n0, K, stream):
+    """Moments through the public API with host buffers: per step, copy the
+    step's inputs (the two previous RBMs, their betas, the walkers) from pinned
+    host memory, run the moment, read back RBM_n, beta_n and mu_n."""
+    import torch
+    P = ctx.P
+    cd = ctx.cdtype
+    h_prev = torch.empty(2, P, dtype=cd).pin_memory()
+    h_beta = torch.empty(2, dtype=torch.complex128).pin_memory()
+    h_spins = torch.empty_like(seq.spins, device="cpu").pin_memory()
+    h_out = torch.empty(P, dtype=cd).pin_memory()
+    h_res = torch.empty(2, dtype=torch.complex128).pin_memory()
+    times = []
+    for k in range(K):
+        n = n0 + k
+        h_prev.copy_(seq.params[n - 2:n])
+        h_beta.copy_(seq.betas[n - 2:n])
+        h_spins.copy_(seq.spins)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        seq.params[n - 2:n].copy_(h_prev, non_blocking=True)
+        seq.betas[n - 2:n].copy_(h_beta, non_blocking=True)
+        seq.spins.copy_(h_spins, non_blocking=True)
+        seq.fit(n)
+        h_out.copy_(seq.params[n], non_blocking=True)
+        h_res[0:1].copy_(seq.betas[n:n + 1], non_blocking=True)
+        h_res[1:2].copy_(seq.mu[n:n + 1], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    item = 8 if cd == torch.complex64 else 16
+    Bi = 2 * P * item + 2 * 16 + seq.spins.numel()
+    Bo = P * item + 2 * 16
+    return float(np.mean(times)), Bi, Bo
+
+
+def oracle_iteration_time(n_walkers, seed=5):
+    """One natural-gradient iteration of the oracle at the full chain64 sizes
+    on n_walkers walkers: sweep, local target, log-derivatives, S, F and the
+    Cholesky solve.  Returns (seconds of the walker-proportional part,
+    seconds of the P x P solve)."""
+    from oracle import lattice, rbm, sampler, sr, target
+    from oracle.target import State
+    from paper_2103_08804_gb300 import synth
+    wl = synth.WORKLOADS[WORKLOAD]
+    E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
+    N, M = wl.N, wl.M
+    psi = synth.rbm_params(seed, N, M, wl.sigma)
+    p1 = synth.rbm_params(seed + 1, N, M, wl.sigma)
+    p2 = synth.rbm_params(seed + 2, N, M, wl.sigma)
+    spins = synth.sz0_spins(seed + 3, n_walkers, N)
+    bl = lattice.bonds(wl.Lx, wl.Ly)
+    t0 = time.perf_counter()
+    spins, _, _ = sampler.mc_sweep(psi, N, M, bl, spins, 1, seed, 0)
+    lp = rbm.logpsi(psi, N, M, spins)
+    R = target.local_target(3, State(p1), State(p2), 0.5, 0.25, N, M, wl.Lx, wl.Ly, 1.0, E0, a,
+                            0.9875, wl.q, spins, lp)
+    O = rbm.logderiv(psi, N, M, spins)
+    est = sr.estimators(O, R)
+    F, _ = sr.force(est, wl.dgamma)
+    S = sr.qgt(est)
+    t1 = time.perf_counter()
+    sr.shifted_solve(S, F, wl.shift)
+    return t1 - t0, time.perf_counter() - t1
+
+
+def _moment_seconds(t_walk, t_solve, n_walkers, wl):
+    # walker-proportional work scales with the walker count, the solve does not
+    return (t_walk * wl.walkers / n_walkers + t_solve) * (wl.iters + 2)
+
+
+def cpu_baseline(args):
+    from paper_2103_08804_gb300 import synth
+    wl = synth.WORKLOADS[WORKLOAD]
+    cores = len(os.sched_getaffinity(0))
+    tw, ts = oracle_iteration_time(args.cpu_walkers)
+    t_moment = _moment_seconds(tw, ts, args.cpu_walkers, wl)
+    return {"value": 3600.0 / t_moment, "unit": "moments/hour", "cores": cores, "kind": "oracle",
+            "sample": f"one natural-gradient iteration of the float64 numpy oracle at N=64, "
+                      f"M=128, P=8384 on {args.cpu_walkers} walkers ({tw:.1f} s sampling, "
+                      f"target and S build; {ts:.1f} s Cholesky solve), walker part scaled to "
+                      f"{wl.walkers} walkers, times {wl.iters + 2} iterations per moment "
+                      f"(extrapolated)"}
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2103_08804_gb300 import synth
+    wl = synth.WORKLOADS[WORKLOAD]
+    cores = len(os.sched_getaffinity(0))
+    nw = args.cpu_walkers
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_iteration_time(256)
+    ts = [oracle_iteration_time(nw, seed=5 + k) for k in range(args.steps)]
+    t_moment = _moment_seconds(float(np.mean([t[0] for t in ts])),
+                               float(np.mean([t[1] for t in ts])), nw, wl)
+    value = 3600.0 / t_moment
+    print(json.dumps({
+        "impl": "reference", "metric": "Chebyshev moments/hour", "value": value,
+        "unit": "moments/hour", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_moment * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "chain64 (see ours)", "walkers_sampled": nw},
+        "cpu_baseline": {"value": value, "unit": "moments/hour", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle iterations on {nw} walkers, scaled "
+                                   f"linearly to {wl.walkers} walkers x {wl.iters + 2} sweeps"},
+        "e2e": {"value": value, "unit": "moments/hour", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,275 @@
+/*
+ * chebrbm.h -- C ABI of the GB300 (sm_103a) hot path of the RBM-Chebyshev
+ * method for spin spectral functions: Hendry, Chen, Weinberg, Feiguin,
+ * "Chebyshev expansion of spectral functions using restricted Boltzmann
+ * machines", arXiv:2103.08804.
+ *
+ * One projection step of the Chebyshev recursion fits a complex RBM psi_n to
+ * the target phi_n = 2 beta_{n-1} H' t~_{n-1} - beta_{n-2} t~_{n-2}
+ * (Sec. III, last paragraph) by the natural-gradient update of Sec. III,
+ * with every expectation sampled from |psi_n|^2.  The calls below are the
+ * steps of that projection in the paper's order:
+ *
+ *   rbm_logpsi        theta and log psi of the RBM ansatz           (Sec. I)
+ *   mc_sweep          Metropolis sampling of |psi_s|^2              (Sec. III)
+ *   cheb_local_target R(s) = phi_s / psi_s over Heisenberg bonds    (Secs. III, V)
+ *   logderiv          O_k(s) = d log psi_s / d alpha_k              (Sec. III)
+ *   logpsi_backward   sum_s g_s conj(O_k(s)), the VJP of log psi    (Sec. III)
+ *   sr_step           <R>, <|R|^2>, <O*>, <O* R>, gamma, F, S and the
+ *                     shifted solve (S + lambda I) dalpha = F      (Sec. III)
+ *   cheb_moment       beta_n, mu_n and the Krylov columns           (Secs. II, IV)
+ *   cheb_gram         sigma_nm = <t_n|t_m>, H_nm = <t_n|H'|t_m>     (Sec. IV)
+ *   cheb_krylov       moment correction and projected eigenproblem  (Secs. IV, V)
+ *
+ * CONVENTIONS
+ *   Memory. Every array argument is a DEVICE pointer owned by the caller,
+ *     unless a comment says "host". The library never frees caller memory.
+ *     The context owns only its workspace, allocated once in cr_create, so
+ *     the hot calls allocate nothing and can be captured in a CUDA graph.
+ *     The one exception is cheb_krylov (called once per sequence), which
+ *     sizes its float64 scratch on first use.
+ *   Streams. Every call is asynchronous on the context's stream; results
+ *     are valid after that stream is synchronised.
+ *   Precision. "complex" arrays are interleaved (re, im) in the context's
+ *     storage precision: complex128 for CR_FP64, complex64 for CR_FP32 and
+ *     CR_MIXED. Results documented as complex128 (beta, mu, F, stats, G, H)
+ *     are complex128 in every mode.
+ *   Parameters. An RBM with N visible and M hidden units is one complex
+ *     vector alpha = [a (N) | b (M) | W (N x M, row-major, W[i*M + j])];
+ *     its index is the k of O_k, S_kk' and F_k. P = N + M + N*M.
+ *   Spins. int8 [B][N], entries +1 / -1, site r = x + Lx*y.
+ *   Lattice. Periodic; bonds are all (r, r + x-hat) in increasing r and
+ *     then, when Ly > 1, all (r, r + y-hat) in increasing r.
+ *   Hamiltonian. H = J sum_b S_i . S_j with S^z = sigma/2 (Sec. V);
+ *     H' = (H - E0)/a - W' (Sec. II).
+ *   Errors. Argument checks return a status synchronously and set the text
+ *     returned by cr_last_error. Failures detected on the device (a
+ *     non-positive Cholesky pivot, non-finite estimators or parameters) set a
+ *     device status word that cr_sync_status reads and clears. CG that stops
+ *     at its iteration limit is not an error: sr_step reports the iteration
+ *     count and residual in its stats.
+ *   B == 0 is valid for every call and launches nothing.
+ */
+#ifndef CHEBRBM_H
+#define CHEBRBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cr_ctx cr_ctx;
+
+typedef enum {
+    CR_OK = 0,
+    CR_EINVAL = 1,      /* bad argument */
+    CR_ENOMEM = 2,      /* workspace allocation failed (cr_create only) */
+    CR_ECUDA = 3,       /* a CUDA runtime call or launch failed */
+    CR_ETIMEOUT = 4,    /* a bounded device wait gave up */
+    CR_ENOTCONV = 5,    /* CG reached its iteration limit above tolerance */
+    CR_ESINGULAR = 6,   /* Cholesky met a non-positive pivot */
+    CR_ENONFINITE = 7   /* NaN or Inf in an estimator */
+} cr_status;
+
+typedef enum {
+    CR_FP64 = 0,        /* everything in float64 */
+    CR_FP32 = 1,        /* float32 storage and arithmetic, float64 sums and solve */
+    CR_MIXED = 2        /* float32 storage; contractions on the tensor cores in
+                           split bf16 (3 terms) with float32 accumulation;
+                           float64 sums and solve */
+} cr_prec;
+
+/* Context flags. */
+#define CR_CTX_EXPLICIT_S 1 /* allocate the explicit P x P complex128 S for
+                               Cholesky solves */
+
+/* Solvers for sr_step. */
+#define CR_SOLVE_CHOLESKY 0 /* explicit S, float64 Cholesky (needs CR_CTX_EXPLICIT_S) */
+#define CR_SOLVE_CG 1       /* matrix-free S v = O^dag (O v) / Ns, float64 CG */
+
+/* Length of the stats array written by sr_step (complex128 / float64 slots). */
+#define CR_STATS_LEN 8
+/* stats layout (float64): [0] gamma, [1] Re <R>, [2] Im <R>, [3] <|R|^2>,
+   [4] c = dgamma * gamma cot gamma, [5] CG iterations, [6] CG relative
+   residual, [7] |F|_2 */
+
+typedef struct {
+    int Lx, Ly;         /* Ly == 1: chain of Lx sites. Needs Lx >= 3 and
+                           Ly == 1 or Ly >= 3. */
+    double J;           /* exchange constant */
+} cr_lattice;
+
+/* A variational state: an RBM, optionally times the probe factor.
+   probe != 0 means t~(sigma) = f_q(sigma) RBM(sigma) with
+   f_q(sigma) = N^{-1/2} sum_r e^{-i q.r} sigma_r / 2, i.e. the exact
+   t_0 = S^z_q psi of Sec. II / Appendix B. */
+typedef struct {
+    const void* params; /* device, complex [P], context precision */
+    int probe;
+    double qx, qy;
+} cr_state;
+
+/* Counter-based random stream (Philox4x32-10, Salmon et al. SC'11).
+   key = seed; counter = (walker, step lo, step hi, 0). Host struct; calls
+   that draw from it advance `counter` on the host, synchronously. */
+typedef struct {
+    uint64_t seed;
+    uint64_t counter;
+} cr_philox;
+
+/* The target of projection step n (Sec. III, last paragraph). */
+typedef struct {
+    int n;                  /* state being fitted, n >= 1 */
+    cr_state prev;          /* t~_{n-1} */
+    cr_state prev2;         /* t~_{n-2}; ignored when n == 1 */
+    const double* beta_prev;  /* device complex128 [1]: beta_{n-1}; beta_0 = 1 */
+    const double* beta_prev2; /* device complex128 [1]: beta_{n-2}; ignored when n == 1 */
+    double E0, a, Wp;       /* H' = (H - E0)/a - W' */
+} cr_target;
+
+typedef struct {
+    double dgamma;          /* rotation fraction delta-gamma of Sec. III */
+    double shift;           /* additive diagonal shift lambda > 0 */
+    int solver;             /* CR_SOLVE_CHOLESKY or CR_SOLVE_CG */
+    int cg_maxit;           /* CG iteration limit (CG only) */
+    double cg_tol;          /* CG stops when |r| <= cg_tol |F| */
+} cr_sr_opts;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context for one lattice and hidden-layer width M.
+   max_walkers bounds B in every later call. flags: CR_CTX_EXPLICIT_S.
+   stream: a cudaStream_t (NULL = legacy default stream).
+   Allocates all workspace; returns CR_ENOMEM / CR_ECUDA on failure. */
+cr_status cr_create(cr_ctx** out, const cr_lattice* lattice, int M, int max_walkers,
+                    cr_prec prec, int flags, void* stream);
+cr_status cr_destroy(cr_ctx* ctx);
+/* Rebind the context to another stream (e.g. a graph-capture stream). */
+cr_status cr_set_stream(cr_ctx* ctx, void* stream);
+/* Text of the last error of this context (static storage in the context). */
+const char* cr_last_error(const cr_ctx* ctx);
+/* Synchronise the context stream, then read and clear the device status
+   word: returns the first device-side error since the last call, or CR_OK. */
+cr_status cr_sync_status(cr_ctx* ctx);
+/* Instrumentation.  cr_n_launches: kernels this context has launched so far
+   (host counter).  cr_time_kernel arms CUDA-event timing of one kernel
+   family (CR_KERNEL_*; -1 disarms): every later launch of it records a
+   start/stop event pair on the context stream, up to `capacity` launches
+   (events are created here, outside any hot call).  cr_kernel_times
+   synchronises the stream and writes the recorded durations in ms (host
+   float [capacity]); returns their count, or -1 on error. */
+#define CR_KERNEL_SWEEP 0   /* Metropolis sweep */
+#define CR_KERNEL_TARGET 1  /* H' application: local target and moment columns */
+#define CR_KERNEL_THETA 2   /* theta = b + sigma W and log psi */
+#define CR_KERNEL_OV 3      /* u = O v (matrix-free S, first half) */
+#define CR_KERNEL_REDUCE 4  /* sum_s op(O_k(s)) g_s (F, Obar, S v second half, VJP) */
+#define CR_KERNEL_CG 5      /* CG vector update */
+long long cr_n_launches(const cr_ctx* ctx);
+cr_status cr_time_kernel(cr_ctx* ctx, int kernel_id, int capacity);
+int cr_kernel_times(cr_ctx* ctx, float* ms_out, int capacity);
+
+/* Sizes: N, M, P, number of bonds. */
+int cr_n_sites(const cr_ctx* ctx);
+int cr_n_hidden(const cr_ctx* ctx);
+int cr_n_params(const cr_ctx* ctx);
+int cr_n_bonds(const cr_ctx* ctx);
+
+/* ------------------------------------------------------------- hot path */
+
+/* Sec. I: theta_j = b_j + sum_i W_ij sigma_i and
+   log psi = sum_i a_i sigma_i + sum_j log(2 cosh theta_j) (principal log per
+   term, so log psi is defined mod 2 pi i). The probe flag of `state` is
+   ignored: this is the RBM factor alone.
+   spins [B][N]; theta_out complex [B][M] or NULL; logpsi_out complex [B]. */
+cr_status rbm_logpsi(cr_ctx* ctx, const cr_state* state, const int8_t* spins, int B,
+                     void* theta_out, void* logpsi_out);
+
+/* Sec. III: Metropolis sampling of |psi_s|^2 / <psi|psi>. Each walker makes
+   n_sweeps * N proposals; a proposal picks a bond uniformly
+   (floor(u0 * N_b / 2^32)) and, if its spins are antiparallel, exchanges them
+   with probability min(1, |psi(s')/psi(s)|^2), accepting iff
+   ((u1 >> 9) + 1/2) / 2^23 < |psi(s')/psi(s)|^2. Proposal p of walker w uses
+   Philox call counter + p/2, words (2(p%2), 2(p%2)+1). rng->counter advances
+   by ceil(n_sweeps * N / 2). Total S^z is conserved.
+   spins [B][N] in/out. theta [B][M] in/out: on entry it must equal
+   b + sigma W for `state` (as written by rbm_logpsi); on exit it matches the
+   new spins. logpsi_out [B] (NULL allowed), tanh_out [B][M] = tanh(theta)
+   (NULL allowed), n_accepted [B] int32 accepted moves in this call (NULL
+   allowed). The probe flag of `state` must be 0. */
+cr_status mc_sweep(cr_ctx* ctx, const cr_state* state, int8_t* spins, void* theta, int B,
+                   int n_sweeps, cr_philox* rng, void* logpsi_out, void* tanh_out,
+                   int32_t* n_accepted);
+
+/* Secs. III and V: R(s) = phi_n(s) / psi_n(s) with
+   phi_1 = beta_0 H' t~_0 and phi_n = 2 beta_{n-1} H' t~_{n-1} - beta_{n-2} t~_{n-2},
+   (H v)(s) = sum_b [(J/4) s_i s_j v(s) + (J/2)[s_i != s_j] v(s^{ij})].
+   spins [B][N] samples of |psi_n|^2, logpsi_n [B] log psi_n at those
+   samples (from mc_sweep or rbm_logpsi), R_out complex [B].  mean_out:
+   device complex128 [1] receiving <R> summed in float64 (this is
+   beta_n = <psi|phi>/<psi|psi> of Sec. III once the fit has converged), or
+   NULL. */
+cr_status cheb_local_target(cr_ctx* ctx, const cr_target* target, const int8_t* spins,
+                            const void* logpsi_n, int B, void* R_out, double* mean_out);
+
+/* Sec. III: O_{a_i} = sigma_i, O_{b_j} = tanh theta_j, O_{W_ij} = sigma_i tanh theta_j.
+   theta [B][M] (from rbm_logpsi / mc_sweep). tanh_out [B][M] (NULL allowed);
+   O_out complex [B][P] explicit log-derivatives (NULL allowed). */
+cr_status logderiv(cr_ctx* ctx, const cr_state* state, const int8_t* spins, const void* theta,
+                   int B, void* tanh_out, void* O_out);
+
+/* Backward of log psi: grad_params[k] = sum_s g_s conj(O_k(s)), i.e. the
+   vector-Jacobian product that gives d L / d conj(alpha) for a real loss L
+   with d L / d conj(log psi_s) = g_s. tanh_theta [B][M], grad_logpsi
+   complex [B], grad_params complex [P] (overwritten). */
+cr_status logpsi_backward(cr_ctx* ctx, const cr_state* state, const int8_t* spins,
+                          const void* tanh_theta, int B, const void* grad_logpsi,
+                          void* grad_params);
+
+/* Sec. III natural-gradient update, on samples of |psi|^2:
+     gamma = arccos sqrt(min(1, |<R>|^2 / <|R|^2>)),
+     F_k   = dgamma * gamma cot gamma * (<O_k* R>/<R> - <O_k*>)   (gamma cot gamma = 1 below 1e-8),
+     S_kk' = <O_k* O_k'> - <O_k>* <O_k'>,
+   then solves (S + shift I) dalpha = F in float64 and sets
+   params += dalpha. params complex [P] in/out (context precision);
+   tanh_theta [B][M] at the samples; R complex [B]; stats_out float64
+   [CR_STATS_LEN] (device) or NULL. */
+cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, const void* tanh_theta,
+                  const void* R, int B, const cr_sr_opts* opts, double* stats_out);
+
+/* Secs. II and IV, on samples s of |psi|^2 of the reference state psi:
+     Bcol[s]  = beta t~(s) / psi(s)              (B_n of the Gram estimator)
+     HBcol[s] = beta (H' t~)(s) / psi(s)          (needs hprime, else NULL)
+     mu[0:2]  = < conj(f_q(s)) Bcol[s] >          complex128, mu_n of Sec. II
+   with f_q the probe factor at momentum (qx, qy). state: t~_n; beta: device
+   complex128 [1]; logpsi_ref [B] log psi at the samples; hprime: host
+   float64 {E0, a, Wp} or NULL. Bcol, HBcol: complex [B] or NULL; mu_out:
+   device complex128 [1] or NULL. */
+cr_status cheb_moment(cr_ctx* ctx, const cr_state* state, const double* beta, double qx,
+                      double qy, const int8_t* spins, const void* logpsi_ref, int B,
+                      const double* hprime, void* Bcol, void* HBcol, double* mu_out);
+
+/* Sec. IV estimators: G_nm = <conj(B_n) B_m>, H_nm = <conj(B_n) HB_m>, then
+   H <- (H + H^dag)/2. Bmat, HBmat complex [Nm][ld] (row n = column B_n over
+   the B samples, leading dimension ld >= B); G_out, H_out complex128
+   [Nm][Nm] (device). */
+cr_status cheb_gram(cr_ctx* ctx, const void* Bmat, const void* HBmat, int Nm, int B, int ld,
+                    double* G_out, double* H_out);
+
+/* Secs. IV and V in float64 on the device: with G^+ the pseudo-inverse of G
+   (eigenvalues below cutoff * max dropped), c_0 = e_0, c_1 = G^+ H c_0,
+   c_{n+1} = G^+ (2 H c_n - G c_{n-1}), mu'_n = (G c_n)_0 for n < n_out; and
+   the projected eigenproblem H c = lambda G c by canonical
+   orthogonalisation, with weights w_k = |<v_k| X^dag G e_0>|^2.
+   G, H complex128 [Nm][Nm]; mu_corr_out complex128 [n_out]; poles_out,
+   weights_out float64 [Nm] (entries past the kept rank are 0); rank_out int32
+   [1] (device) or NULL. Nm <= 512. */
+cr_status cheb_krylov(cr_ctx* ctx, const double* G, const double* H, int Nm, double cutoff,
+                      int n_out, double* mu_corr_out, double* poles_out, double* weights_out,
+                      int32_t* rank_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEBRBM_H */

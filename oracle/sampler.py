@@ -24,15 +24,17 @@ def n_calls(n_sweeps, N):
     return (n_sweeps * N + 1) // 2
 
 
-def mc_sweep(params, N, M, bonds, spins, n_sweeps, seed, counter):
+def mc_sweep(params, N, M, bonds, spins, n_sweeps, seed, counter, walker_ids=None):
     """Run n_sweeps * N exchange proposals on every walker.
 
-    spins   int8 [B, N], +-1 (not modified; a new array is returned)
+    spins       int8 [B, N], +-1 (not modified; a new array is returned)
+    walker_ids  the walker index of each row in the random stream (default
+                0..B-1), so that a subset of a large batch can be replayed
     returns (new spins, accepted-move count per walker, advanced counter)
     """
     spins = np.array(spins, dtype=np.int8, copy=True)
     B = spins.shape[0]
-    walkers = np.arange(B, dtype=np.uint64)
+    walkers = (np.arange(B) if walker_ids is None else np.asarray(walker_ids)).astype(np.uint64)
     rows = np.arange(B)
     lp = logpsi(params, N, M, spins)
     accepted = np.zeros(B, dtype=np.int64)

@@ -1,0 +1,210 @@
+// Context lifetime, workspace and status handling.
+#include <stdarg.h>
+#include <stdlib.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+cr_status cr_fail(cr_ctx* c, cr_status s, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+bool cr_kt_begin(cr_ctx* c, int kid) {
+    if (kid < 0 || c->kt.kid != kid || c->kt.count >= c->kt.cap) return false;
+    cudaEventRecord(c->kt.ev[2 * c->kt.count], c->stream);
+    return true;
+}
+
+void cr_kt_end(cr_ctx* c) {
+    cudaEventRecord(c->kt.ev[2 * c->kt.count + 1], c->stream);
+    ++c->kt.count;
+}
+
+static void kt_free(cr_ctx* c) {
+    if (c->kt.ev) {
+        for (int i = 0; i < 2 * c->kt.cap; ++i) cudaEventDestroy(c->kt.ev[i]);
+        free(c->kt.ev);
+    }
+    c->kt.ev = nullptr;
+    c->kt.cap = c->kt.count = 0;
+    c->kt.kid = -1;
+}
+
+extern "C" long long cr_n_launches(const cr_ctx* c) { return c ? c->n_launches : -1; }
+
+extern "C" cr_status cr_time_kernel(cr_ctx* c, int kid, int cap) {
+    if (!c) return CR_EINVAL;
+    kt_free(c);
+    if (kid < 0) return CR_OK;
+    if (cap < 1) return cr_fail(c, CR_EINVAL, "cr_time_kernel: capacity < 1");
+    c->kt.ev = (cudaEvent_t*)calloc(2 * (size_t)cap, sizeof(cudaEvent_t));
+    if (!c->kt.ev) return CR_ENOMEM;
+    for (int i = 0; i < 2 * cap; ++i)
+        if (cudaEventCreate(&c->kt.ev[i]) != cudaSuccess) {
+            c->kt.cap = i / 2;
+            kt_free(c);
+            return cr_fail(c, CR_ECUDA, "cr_time_kernel: event creation failed");
+        }
+    c->kt.cap = cap;
+    c->kt.count = 0;
+    c->kt.kid = kid;
+    return CR_OK;
+}
+
+extern "C" int cr_kernel_times(cr_ctx* c, float* ms, int cap) {
+    if (!c || !ms) return -1;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return -1;
+    int n = c->kt.count < cap ? c->kt.count : cap;
+    for (int i = 0; i < n; ++i)
+        if (cudaEventElapsedTime(&ms[i], c->kt.ev[2 * i], c->kt.ev[2 * i + 1]) != cudaSuccess)
+            return -1;
+    return n;
+}
+
+cr_status cr_check_launch(cr_ctx* c, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cr_fail(c, CR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return CR_OK;
+}
+
+// Periodic nearest-neighbour bonds: (r, r + x-hat) for all r, then
+// (r, r + y-hat) for all r when Ly > 1 (Sec. V: nearest neighbours, PBC).
+static std::vector<int2> make_bonds(int Lx, int Ly) {
+    std::vector<int2> b;
+    for (int y = 0; y < Ly; ++y)
+        for (int x = 0; x < Lx; ++x) b.push_back(make_int2(x + Lx * y, (x + 1) % Lx + Lx * y));
+    if (Ly > 1)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x) b.push_back(make_int2(x + Lx * y, x + Lx * ((y + 1) % Ly)));
+    return b;
+}
+
+static cudaError_t alloc(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    return cudaMalloc(p, bytes);
+}
+
+extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int max_walkers,
+                               cr_prec prec, int flags, void* stream) {
+    if (!out || !lat) return CR_EINVAL;
+    *out = nullptr;
+    if (lat->Lx < 3 || lat->Ly < 1 || (lat->Ly != 1 && lat->Ly < 3)) return CR_EINVAL;
+    if (M < 1 || M > 512 || max_walkers < 1) return CR_EINVAL;
+    if (prec != CR_FP64 && prec != CR_FP32 && prec != CR_MIXED) return CR_EINVAL;
+    cr_ctx* c = (cr_ctx*)calloc(1, sizeof(cr_ctx));
+    if (!c) return CR_ENOMEM;
+    c->Lx = lat->Lx;
+    c->Ly = lat->Ly;
+    c->N = lat->Lx * lat->Ly;
+    c->M = M;
+    // hidden units padded to 32 lanes x a power-of-two run per lane
+    int kpl = 1;
+    while (32 * kpl < M) kpl *= 2;
+    c->Mp = 32 * kpl;
+    c->Nb = lat->Ly == 1 ? c->N : 2 * c->N;
+    c->P = c->N + M + c->N * M;
+    c->J = lat->J;
+    c->prec = prec;
+    c->max_walkers = max_walkers;
+    c->flags = flags;
+    c->stream = (cudaStream_t)stream;
+    c->kt.kid = -1;
+    c->n_chunks = (max_walkers + 255) / 256;
+    if (c->n_chunks > 64) c->n_chunks = 64;
+    if (c->N > 1024 || c->N % 2) {
+        free(c);
+        return CR_EINVAL;
+    }
+    const size_t rs = rsize(c), cs = 2 * rs;
+    const size_t P = c->P, Nb = c->Nb, Mp = c->Mp, B = max_walkers;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes)                                 \
+    if (e == cudaSuccess) e = alloc((void**)&(ptr), (bytes))
+    ALLOC(c->d_status, sizeof(int));
+    ALLOC(c->d_bonds, Nb * sizeof(int2));
+    for (int s = 0; s < 2; ++s) {
+        ALLOC(c->tab[s].D, Nb * Mp * cs);
+        ALLOC(c->tab[s].Ch, Nb * Mp * cs);
+        ALLOC(c->tab[s].Sh, Nb * Mp * cs);
+        ALLOC(c->tab[s].ChT, Nb * Mp * cs);
+        ALLOC(c->tab[s].ShT, Nb * Mp * cs);
+        ALLOC(c->tab[s].ea, Nb * 2 * cs);
+    }
+    ALLOC(c->theta_tmp, B * M * cs);
+    ALLOC(c->lp_tmp, 2 * B * cs);
+    ALLOC(c->u_tmp, B * cs);
+    ALLOC(c->partial, (size_t)c->n_chunks * (P + 2) * 16);
+    ALLOC(c->red, 3 * (P + 2) * 16);
+    ALLOC(c->F, P * 16);
+    ALLOC(c->cg, 4 * P * 16);
+    ALLOC(c->p_lo, P * cs);
+    ALLOC(c->scal, 64 * sizeof(double));
+    if (flags & CR_CTX_EXPLICIT_S) {
+        ALLOC(c->S, P * P * 16);
+        ALLOC(c->O_tmp, B * P * cs);
+    }
+#undef ALLOC
+    if (e != cudaSuccess) {
+        cr_destroy(c);
+        return e == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;
+    }
+    std::vector<int2> bonds = make_bonds(c->Lx, c->Ly);
+    e = cudaMemcpy(c->d_bonds, bonds.data(), Nb * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->scal, 0, 64 * sizeof(double));
+    if (e != cudaSuccess) {
+        cr_destroy(c);
+        return CR_ECUDA;
+    }
+    *out = c;
+    return CR_OK;
+}
+
+extern "C" cr_status cr_destroy(cr_ctx* c) {
+    if (!c) return CR_EINVAL;
+    kt_free(c);
+    void* ptrs[] = {c->d_status, c->d_bonds, c->theta_tmp, c->lp_tmp, c->u_tmp, c->partial,
+                    c->red, c->F, c->cg, c->p_lo, c->scal, c->S, c->O_tmp, c->kry};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int s = 0; s < 2; ++s) {
+        void* t[] = {c->tab[s].D, c->tab[s].Ch, c->tab[s].Sh, c->tab[s].ChT, c->tab[s].ShT,
+                     c->tab[s].ea};
+        for (void* p : t)
+            if (p) cudaFree(p);
+    }
+    free(c);
+    return CR_OK;
+}
+
+extern "C" cr_status cr_set_stream(cr_ctx* c, void* stream) {
+    if (!c) return CR_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return CR_OK;
+}
+
+extern "C" const char* cr_last_error(const cr_ctx* c) { return c ? c->err : "null context"; }
+
+extern "C" cr_status cr_sync_status(cr_ctx* c) {
+    if (!c) return CR_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cr_fail(c, CR_ECUDA, "stream sync: %s", cudaGetErrorString(e));
+    int st = 0;
+    e = cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cr_fail(c, CR_ECUDA, "status read: %s", cudaGetErrorString(e));
+    if (st) cr_fail(c, (cr_status)st, "device status %d", st);
+    return (cr_status)st;
+}
+
+extern "C" int cr_n_sites(const cr_ctx* c) { return c ? c->N : -1; }
+extern "C" int cr_n_hidden(const cr_ctx* c) { return c ? c->M : -1; }
+extern "C" int cr_n_params(const cr_ctx* c) { return c ? c->P : -1; }
+extern "C" int cr_n_bonds(const cr_ctx* c) { return c ? c->Nb : -1; }

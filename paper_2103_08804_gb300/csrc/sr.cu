@@ -1,0 +1,525 @@
+// The natural-gradient update of Sec. III on samples of |psi|^2:
+//   S_kk' = <O_k* O_k'> - <O_k>* <O_k'>
+//   gamma = arccos sqrt(|<R>|^2 / <|R|^2>)
+//   F_k   = dgamma gamma cot(gamma) (<O_k* R> / <R> - <O_k*>)
+//   (S + lambda I) dalpha = F,  alpha <- alpha + dalpha
+// and the VJP of log psi.  O is never stored on the matrix-free path: it is
+// rebuilt on the fly from (sigma, tanh theta) with O_a = sigma, O_b = T,
+// O_W = sigma (x) T.  Products run in the context precision; every sum over
+// walkers is finished in float64 in a fixed order, so results are
+// reproducible run to run.
+#include "common.cuh"
+
+cr_status launch_ov(cr_ctx* c, const void* v, const int8_t* spins, int B, const void* T, void* u,
+                    const double* skip);
+cr_status logderiv_impl(cr_ctx* ctx, const int8_t* spins, const void* theta, int B, void* tanh_out,
+                        void* O_out);
+
+// ------------------------------------------------------------ reductions
+//
+// partial[c][k] = sum over walker chunk c of op(O_k(s)) g_s, k < P, with
+// op = conj or identity, g_s = 1 when g is null; partial[c][P] = sum g_s,
+// partial[c][P+1] = sum |g_s|^2.  Grid (chunk, i-tile): thread t owns hidden
+// units j = t + 128 k and the IT visible units of its tile for O_W; CTAs of
+// tile 0 also produce the a, b and scalar sums.
+template <typename R, int JPT, int IT, bool CONJ>
+__global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__ spins,
+                                                      const cpx<R>* __restrict__ T,
+                                                      const cpx<R>* __restrict__ g, int B, int N,
+                                                      int M, int P, int chunk,
+                                                      double* __restrict__ partial,
+                                                      const double* __restrict__ skip) {
+    if (skip && *skip != 0.0) return;
+    constexpr int SUB = 32;
+    __shared__ R sg[SUB][IT];
+    __shared__ cpx<R> gs[SUB];
+    const int c = blockIdx.x, i0 = blockIdx.y * IT, t = threadIdx.x;
+    const int s0 = c * chunk, s1 = min(B, s0 + chunk);
+    cpx<R> accW[IT][JPT], accb[JPT];
+#pragma unroll
+    for (int k = 0; k < JPT; ++k) {
+        accb[k] = {R(0), R(0)};
+#pragma unroll
+        for (int ii = 0; ii < IT; ++ii) accW[ii][k] = {R(0), R(0)};
+    }
+    cpx<R> acca = {R(0), R(0)}, accg = {R(0), R(0)};
+    R accgg = R(0);
+    for (int sb = s0; sb < s1; sb += SUB) {
+        __syncthreads();
+        for (int e = t; e < SUB * IT; e += 128) {
+            int s = sb + e / IT, i = i0 + e % IT;
+            sg[e / IT][e % IT] = (s < s1 && i < N) ? R(spins[(size_t)s * N + i]) : R(0);
+        }
+        if (t < SUB) {
+            int s = sb + t;
+            gs[t] = s < s1 ? (g ? g[s] : cpx<R>{R(1), R(0)}) : cpx<R>{R(0), R(0)};
+        }
+        __syncthreads();
+        const int ns = min(SUB, s1 - sb);
+        for (int q = 0; q < ns; ++q) {
+            const cpx<R> gq = gs[q];
+            const int s = sb + q;
+#pragma unroll
+            for (int k = 0; k < JPT; ++k) {
+                int j = t + 128 * k;
+                if (j < M) {
+                    cpx<R> tv = T[(size_t)s * M + j];
+                    if (CONJ) tv = conj(tv);
+                    cpx<R> y = tv * gq;
+                    accb[k] = accb[k] + y;
+#pragma unroll
+                    for (int ii = 0; ii < IT; ++ii) {
+                        R sv = sg[q][ii];
+                        accW[ii][k].x = fma(sv, y.x, accW[ii][k].x);
+                        accW[ii][k].y = fma(sv, y.y, accW[ii][k].y);
+                    }
+                }
+            }
+            if (t < IT) acca = acca + sg[q][t] * gq;
+            if (t == IT) {
+                accg = accg + gq;
+                accgg += abs2(gq);
+            }
+        }
+    }
+    cpx<double>* out = (cpx<double>*)partial + (size_t)c * (P + 2);
+#pragma unroll
+    for (int k = 0; k < JPT; ++k) {
+        int j = t + 128 * k;
+        if (j < M) {
+#pragma unroll
+            for (int ii = 0; ii < IT; ++ii)
+                if (i0 + ii < N) out[N + M + (size_t)(i0 + ii) * M + j] = ccast<double>(accW[ii][k]);
+            if (blockIdx.y == 0) out[N + j] = ccast<double>(accb[k]);
+        }
+    }
+    if (t < IT && i0 + t < N) out[i0 + t] = ccast<double>(acca);
+    if (blockIdx.y == 0 && t == IT) {
+        out[P] = ccast<double>(accg);
+        out[P + 1] = {(double)accgg, 0.0};
+    }
+}
+
+// red[k] = sum over chunks of partial[c][k], in chunk order.
+__global__ void combine_kernel(const double* __restrict__ partial, int n_chunks, int len,
+                               double* __restrict__ red, const double* __restrict__ skip) {
+    if (skip && *skip != 0.0) return;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= len) return;
+    const cpx<double>* p = (const cpx<double>*)partial;
+    cpx<double> s = {0.0, 0.0};
+    for (int c = 0; c < n_chunks; ++c) s = s + p[(size_t)c * len + k];
+    ((cpx<double>*)red)[k] = s;
+}
+
+template <typename R, bool CONJ>
+static cr_status oreduce_t(cr_ctx* c, const int8_t* spins, const void* T, const void* g, int B,
+                           double* red_out, const double* skip) {
+    const int N = c->N, M = c->M, P = c->P;
+    const int nch = c->n_chunks < B ? c->n_chunks : B;
+    const int chunk = (B + nch - 1) / nch;
+    const int jpt = (M + 127) / 128;
+    const bool dbl = sizeof(R) == 8;
+#define LAUNCH(JPT, IT)                                                                            \
+    CR_LAUNCH(c, CR_KERNEL_REDUCE, oreduce_kernel<R, JPT, IT, CONJ><<<dim3(nch, (N + IT - 1) / IT), 128, 0, c->stream>>>(        \
+        spins, (const cpx<R>*)T, (const cpx<R>*)g, B, N, M, P, chunk, c->partial, skip))
+    if (jpt == 1) {
+        if (dbl) LAUNCH(1, 8); else LAUNCH(1, 16);
+    } else if (jpt == 2) {
+        if (dbl) LAUNCH(2, 4); else LAUNCH(2, 8);
+    } else {
+        if (dbl) LAUNCH(4, 2); else LAUNCH(4, 4);
+    }
+#undef LAUNCH
+    cr_status s = cr_check_launch(c, "oreduce_kernel");
+    if (s != CR_OK) return s;
+    CR_LAUNCH(c, CR_K_OTHER, combine_kernel<<<(P + 2 + 255) / 256, 256, 0, c->stream>>>(c->partial, nch, P + 2, red_out,
+                                                                skip));
+    return cr_check_launch(c, "combine_kernel");
+}
+
+static cr_status oreduce(cr_ctx* c, bool conj_, const int8_t* spins, const void* T, const void* g,
+                         int B, double* red_out, const double* skip) {
+    if (c->prec == CR_FP64)
+        return conj_ ? oreduce_t<double, true>(c, spins, T, g, B, red_out, skip)
+                     : oreduce_t<double, false>(c, spins, T, g, B, red_out, skip);
+    return conj_ ? oreduce_t<float, true>(c, spins, T, g, B, red_out, skip)
+                 : oreduce_t<float, false>(c, spins, T, g, B, red_out, skip);
+}
+
+// ----------------------------------------------------------------- force
+//
+// From redR = [sum conj(O) R | sum R | sum |R|^2] and redO = [sum O | ...]:
+// <R>, <|R|^2>, gamma (argument clamped to <= 1), c = dgamma gamma cot gamma
+// (1 below 1e-8), F_k = c (<O_k* R>/<R> - conj(<O_k>)).
+__device__ void force_scalars(const cpx<double>* redR, int P, int B, double dgamma, cpx<double>* mR,
+                              double* mRR, double* gamma, double* cc) {
+    const double inv = 1.0 / B;
+    *mR = inv * redR[P];
+    *mRR = redR[P + 1].x * inv;
+    double ratio = abs2(*mR) / *mRR;
+    if (!(ratio <= 1.0)) ratio = ratio > 1.0 ? 1.0 : ratio;
+    *gamma = acos(sqrt(ratio));
+    *cc = dgamma * (*gamma < 1e-8 ? 1.0 : *gamma / tan(*gamma));
+}
+
+__global__ void force_kernel(const double* __restrict__ redR_, const double* __restrict__ redO_,
+                             int P, int B, double dgamma, double* __restrict__ F_,
+                             double* __restrict__ stats, int* __restrict__ status) {
+    const cpx<double>* redR = (const cpx<double>*)redR_;
+    const cpx<double>* redO = (const cpx<double>*)redO_;
+    cpx<double> mR;
+    double mRR, gamma, cc;
+    force_scalars(redR, P, B, dgamma, &mR, &mRR, &gamma, &cc);
+    const double inv = 1.0 / B;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P) {
+        cpx<double> f = cdiv(inv * redR[k], mR) - conj(inv * redO[k]);
+        ((cpx<double>*)F_)[k] = cc * f;
+    }
+    if (k == 0) {
+        if (!isfinite(mR.x) || !isfinite(mR.y) || !isfinite(mRR) || abs2(mR) == 0.0)
+            set_status(status, CR_ENONFINITE);
+        if (stats) {
+            stats[0] = gamma;
+            stats[1] = mR.x;
+            stats[2] = mR.y;
+            stats[3] = mRR;
+            stats[4] = cc;
+        }
+    }
+}
+
+// ------------------------------------------------------ explicit S (small P)
+
+template <typename R>
+__global__ void o_from_tanh_kernel(const int8_t* __restrict__ spins, const cpx<R>* __restrict__ T,
+                                   int B, int N, int M, int P, cpx<R>* __restrict__ O) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)B * P) return;
+    int s = (int)(idx / P), k = (int)(idx % P);
+    cpx<R> v;
+    if (k < N) v = {R(spins[(size_t)s * N + k]), R(0)};
+    else if (k < N + M) v = T[(size_t)s * M + (k - N)];
+    else {
+        int i = (k - N - M) / M, j = (k - N - M) % M;
+        v = R(spins[(size_t)s * N + i]) * T[(size_t)s * M + j];
+    }
+    O[idx] = v;
+}
+
+// S[k][l] = sum_s conj(O_sk) O_sl / B - conj(Obar_k) Obar_l + shift delta_kl, float64.
+template <typename R>
+__global__ void sbuild_kernel(const cpx<R>* __restrict__ O, int B, int P,
+                              const double* __restrict__ redO_, double shift,
+                              double* __restrict__ S_) {
+    __shared__ cpx<R> tk[16][17], tl[16][17];
+    const int k = blockIdx.y * 16 + threadIdx.y, l = blockIdx.x * 16 + threadIdx.x;
+    cpx<double> acc = {0.0, 0.0};
+    for (int s0 = 0; s0 < B; s0 += 16) {
+        int s = s0 + threadIdx.x;
+        int kk = blockIdx.y * 16 + threadIdx.y;
+        tk[threadIdx.y][threadIdx.x] = (s < B && kk < P) ? O[(size_t)s * P + kk] : cpx<R>{R(0), R(0)};
+        s = s0 + threadIdx.y;
+        tl[threadIdx.y][threadIdx.x] = (s < B && l < P) ? O[(size_t)s * P + l] : cpx<R>{R(0), R(0)};
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            acc = acc + ccast<double>(cmulc(tk[threadIdx.y][q], tl[q][threadIdx.x]));
+        __syncthreads();
+    }
+    if (k < P && l < P) {
+        const cpx<double>* redO = (const cpx<double>*)redO_;
+        const double inv = 1.0 / B;
+        cpx<double> v = inv * acc - cmulc(inv * redO[k], inv * redO[l]);
+        if (k == l) v.x += shift;
+        ((cpx<double>*)S_)[(size_t)k * P + l] = v;
+    }
+}
+
+// In-place Cholesky S = L L^dag (lower triangle), one CTA, then
+// L y = F, L^dag x = y; x written to out.  Column-oriented so each step is
+// one parallel update and one barrier.
+__global__ void __launch_bounds__(1024) chol_solve_kernel(double* __restrict__ S_, int P,
+                                                          const double* __restrict__ F_,
+                                                          double* __restrict__ x_,
+                                                          int* __restrict__ status) {
+    cpx<double>* S = (cpx<double>*)S_;
+    cpx<double>* x = (cpx<double>*)x_;
+    const cpx<double>* F = (const cpx<double>*)F_;
+    __shared__ double piv;
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    // right-looking factorisation
+    for (int j = 0; j < P; ++j) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double d = S[(size_t)j * P + j].x;
+            if (!(d > 0.0)) {
+                bad = 1;
+                d = 1.0;
+            }
+            piv = sqrt(d);
+            S[(size_t)j * P + j] = {piv, 0.0};
+        }
+        __syncthreads();
+        const double ip = 1.0 / piv;
+        for (int i = j + 1 + threadIdx.x; i < P; i += blockDim.x)
+            S[(size_t)i * P + j] = ip * S[(size_t)i * P + j];
+        __syncthreads();
+        // trailing update of the lower triangle: S_il -= L_ij conj(L_lj), l <= i
+        const int n = P - j - 1;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            int i = j + 1 + e / n, l = j + 1 + e % n;
+            if (l <= i) S[(size_t)i * P + l] = S[(size_t)i * P + l] -
+                                               S[(size_t)i * P + j] * conj(S[(size_t)l * P + j]);
+        }
+    }
+    __syncthreads();
+    if (bad) {
+        if (threadIdx.x == 0) set_status(status, CR_ESINGULAR);
+    }
+    for (int i = threadIdx.x; i < P; i += blockDim.x) x[i] = F[i];
+    // forward: L y = F
+    for (int k = 0; k < P; ++k) {
+        __syncthreads();
+        cpx<double> yk = (1.0 / S[(size_t)k * P + k].x) * x[k];
+        __syncthreads();
+        if (threadIdx.x == 0) x[k] = yk;
+        for (int i = k + 1 + threadIdx.x; i < P; i += blockDim.x)
+            x[i] = x[i] - S[(size_t)i * P + k] * yk;
+    }
+    // backward: L^dag x = y
+    for (int k = P - 1; k >= 0; --k) {
+        __syncthreads();
+        cpx<double> xk = (1.0 / S[(size_t)k * P + k].x) * x[k];
+        __syncthreads();
+        if (threadIdx.x == 0) x[k] = xk;
+        for (int i = threadIdx.x; i < k; i += blockDim.x)
+            x[i] = x[i] - conj(S[(size_t)k * P + i]) * xk;
+    }
+}
+
+// ------------------------------------------------------------------- CG
+//
+// Matrix-free S v = (O^dag (O v) - conj(Obar) sum_s (O v)_s) / B, using
+// sum_s (O_s - Obar) = 0.  Vectors x, r, p, Ap and all scalars in float64;
+// the O-products run in the context precision.  scal: [0] r.r, [1] F.F,
+// [2] done flag, [3] iterations.
+
+template <typename R>
+__global__ void __launch_bounds__(1024) cg_init_kernel(const double* __restrict__ F_, int P,
+                                                       double* __restrict__ cg_,
+                                                       cpx<R>* __restrict__ p_lo,
+                                                       double* __restrict__ scal) {
+    const cpx<double>* F = (const cpx<double>*)F_;
+    cpx<double>* x = (cpx<double>*)cg_;
+    cpx<double>* r = x + P;
+    cpx<double>* p = x + 2 * P;
+    __shared__ double red[32];
+    double rr = 0.0;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        cpx<double> f = F[k];
+        x[k] = {0.0, 0.0};
+        r[k] = f;
+        p[k] = f;
+        p_lo[k] = ccast<R>(f);
+        rr += abs2(f);
+    }
+    rr = warp_sum(rr);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        scal[0] = t;
+        scal[1] = t;
+        scal[2] = t == 0.0 ? 1.0 : 0.0;
+        scal[3] = 0.0;
+    }
+}
+
+__device__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+// One CG step after red = [sum conj(O) u | sum u | .] for u = O p.
+template <typename R>
+__global__ void __launch_bounds__(1024) cg_step_kernel(const double* __restrict__ red_,
+                                                       const double* __restrict__ redO_, int P,
+                                                       int B, double shift, double tol,
+                                                       double* __restrict__ cg_,
+                                                       cpx<R>* __restrict__ p_lo,
+                                                       double* __restrict__ scal) {
+    if (scal[2] != 0.0) return;
+    __shared__ double red[32];
+    const cpx<double>* sOu = (const cpx<double>*)red_;
+    const cpx<double>* sO = (const cpx<double>*)redO_;
+    cpx<double>* x = (cpx<double>*)cg_;
+    cpx<double>* r = x + P;
+    cpx<double>* p = x + 2 * P;
+    cpx<double>* Ap = x + 3 * P;
+    const double inv = 1.0 / B;
+    const cpx<double> mu = inv * sOu[P];
+    double pap = 0.0;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        cpx<double> a = inv * sOu[k] - conj(inv * sO[k]) * mu + shift * p[k];
+        Ap[k] = a;
+        pap += cmulc(p[k], a).x;
+    }
+    pap = block_sum(pap, red);
+    const double rr = scal[0];
+    const double alpha = rr / pap;
+    double rn = 0.0;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        x[k] = x[k] + alpha * p[k];
+        cpx<double> rk = r[k] - alpha * Ap[k];
+        r[k] = rk;
+        rn += abs2(rk);
+    }
+    rn = block_sum(rn, red);
+    const double beta = rn / rr;
+    const bool done = !(rn > tol * tol * scal[1]);
+    if (!done)
+        for (int k = threadIdx.x; k < P; k += blockDim.x) {
+            cpx<double> pk = r[k] + beta * p[k];
+            p[k] = pk;
+            p_lo[k] = ccast<R>(pk);
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        scal[0] = rn;
+        scal[3] += 1.0;
+        if (done) scal[2] = 1.0;
+    }
+}
+
+template <typename R>
+__global__ void apply_update_kernel(cpx<R>* __restrict__ prm, const double* __restrict__ x_, int P,
+                                    const double* __restrict__ scal, double* __restrict__ stats,
+                                    const double* __restrict__ F_, int* __restrict__ status,
+                                    int cg) {
+    const cpx<double>* x = (const cpx<double>*)x_;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P) {
+        cpx<double> v = ccast<double>(prm[k]) + x[k];
+        if (!isfinite(v.x) || !isfinite(v.y)) set_status(status, CR_ENONFINITE);
+        prm[k] = ccast<R>(v);
+    }
+    if (k == 0 && stats) {
+        stats[5] = cg ? scal[3] : 0.0;
+        stats[6] = cg ? (scal[1] > 0 ? sqrt(scal[0] / scal[1]) : 0.0) : 0.0;
+        stats[7] = sqrt(scal[1]);
+    }
+}
+
+__global__ void fnorm_kernel(const double* __restrict__ F_, int P, double* __restrict__ scal) {
+    __shared__ double red[32];
+    const cpx<double>* F = (const cpx<double>*)F_;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) s += abs2(F[k]);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) scal[1] = s;
+}
+
+template <typename R>
+static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const void* T,
+                           const void* Rv, int B, const cr_sr_opts* o, double* stats) {
+    const int P = c->P;
+    double* redR = c->red;
+    double* redO = c->red + 2 * (P + 2);
+    double* redU = c->red + 4 * (P + 2);
+    cr_status s = oreduce(c, true, spins, T, Rv, B, redR, nullptr);
+    if (s != CR_OK) return s;
+    s = oreduce(c, false, spins, T, nullptr, B, redO, nullptr);
+    if (s != CR_OK) return s;
+    CR_LAUNCH(c, CR_K_OTHER, force_kernel<<<(P + 255) / 256, 256, 0, c->stream>>>(redR, redO, P, B, o->dgamma, c->F, stats,
+                                                          c->d_status));
+    if ((s = cr_check_launch(c, "force_kernel")) != CR_OK) return s;
+    double* x = c->cg;
+    if (o->solver == CR_SOLVE_CHOLESKY) {
+        size_t n = (size_t)B * P;
+        CR_LAUNCH(c, CR_K_OTHER, o_from_tanh_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+            spins, (const cpx<R>*)T, B, c->N, c->M, P, (cpx<R>*)c->O_tmp));
+        dim3 g((P + 15) / 16, (P + 15) / 16);
+        CR_LAUNCH(c, CR_K_OTHER, sbuild_kernel<R><<<g, dim3(16, 16), 0, c->stream>>>((const cpx<R>*)c->O_tmp, B, P, redO,
+                                                            o->shift, c->S));
+        CR_LAUNCH(c, CR_K_OTHER, chol_solve_kernel<<<1, 1024, 0, c->stream>>>(c->S, P, c->F, x, c->d_status));
+        CR_LAUNCH(c, CR_K_OTHER, fnorm_kernel<<<1, 1024, 0, c->stream>>>(c->F, P, c->scal));
+        if ((s = cr_check_launch(c, "cholesky path")) != CR_OK) return s;
+    } else {
+        CR_LAUNCH(c, CR_K_OTHER, cg_init_kernel<R><<<1, 1024, 0, c->stream>>>(c->F, P, c->cg, (cpx<R>*)c->p_lo, c->scal));
+        if ((s = cr_check_launch(c, "cg_init")) != CR_OK) return s;
+        const double* done = c->scal + 2;
+        for (int it = 0; it < o->cg_maxit; ++it) {
+            s = launch_ov(c, c->p_lo, spins, B, T, c->u_tmp, done);
+            if (s != CR_OK) return s;
+            s = oreduce(c, true, spins, T, c->u_tmp, B, redU, done);
+            if (s != CR_OK) return s;
+            CR_LAUNCH(c, CR_KERNEL_CG, cg_step_kernel<R><<<1, 1024, 0, c->stream>>>(redU, redO, P, B, o->shift, o->cg_tol,
+                                                         c->cg, (cpx<R>*)c->p_lo, c->scal));
+            if ((s = cr_check_launch(c, "cg_step")) != CR_OK) return s;
+        }
+    }
+    CR_LAUNCH(c, CR_K_OTHER, apply_update_kernel<R><<<(P + 255) / 256, 256, 0, c->stream>>>(
+        (cpx<R>*)params, x, P, c->scal, stats, c->F, c->d_status, o->solver == CR_SOLVE_CG));
+    return cr_check_launch(c, "apply_update");
+}
+
+extern "C" cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, const void* tanh_theta,
+                             const void* R, int B, const cr_sr_opts* opts, double* stats_out) {
+    if (!ctx) return CR_EINVAL;
+    CR_CHECK_ARG(params && opts, "sr_step: null params or opts");
+    CR_CHECK_ARG(B >= 1 && B <= ctx->max_walkers, "sr_step: B=%d outside [1, %d]", B,
+                 ctx->max_walkers);
+    CR_CHECK_ARG(spins && tanh_theta && R, "sr_step: null array");
+    CR_CHECK_ARG(opts->shift > 0.0, "sr_step: shift must be > 0");
+    CR_CHECK_ARG(opts->solver == CR_SOLVE_CHOLESKY || opts->solver == CR_SOLVE_CG,
+                 "sr_step: unknown solver");
+    CR_CHECK_ARG(opts->solver != CR_SOLVE_CHOLESKY || (ctx->flags & CR_CTX_EXPLICIT_S),
+                 "sr_step: Cholesky needs a context created with CR_CTX_EXPLICIT_S");
+    CR_CHECK_ARG(opts->solver != CR_SOLVE_CG || (opts->cg_maxit >= 1 && opts->cg_tol >= 0.0),
+                 "sr_step: bad CG options");
+    return ctx->prec == CR_FP64
+               ? sr_step_t<double>(ctx, params, spins, tanh_theta, R, B, opts, stats_out)
+               : sr_step_t<float>(ctx, params, spins, tanh_theta, R, B, opts, stats_out);
+}
+
+// ------------------------------------------------------ backward of log psi
+
+template <typename R>
+__global__ void to_params_kernel(const double* __restrict__ red_, int P, cpx<R>* __restrict__ out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P) out[k] = ccast<R>(((const cpx<double>*)red_)[k]);
+}
+
+extern "C" cr_status logpsi_backward(cr_ctx* ctx, const cr_state* st, const int8_t* spins,
+                                     const void* tanh_theta, int B, const void* grad_logpsi,
+                                     void* grad_params) {
+    if (!ctx) return CR_EINVAL;
+    CR_CHECK_ARG(st && grad_params, "logpsi_backward: null state or output");
+    CR_CHECK_ARG(B >= 0 && B <= ctx->max_walkers, "logpsi_backward: B=%d outside [0, %d]", B,
+                 ctx->max_walkers);
+    const int P = ctx->P;
+    if (B == 0) {
+        cudaError_t e = cudaMemsetAsync(grad_params, 0, (size_t)P * 2 * rsize(ctx), ctx->stream);
+        return e == cudaSuccess ? CR_OK : cr_fail(ctx, CR_ECUDA, "memset: %s", cudaGetErrorString(e));
+    }
+    CR_CHECK_ARG(spins && tanh_theta && grad_logpsi, "logpsi_backward: null array");
+    double* red = ctx->red;
+    cr_status s = oreduce(ctx, true, spins, tanh_theta, grad_logpsi, B, red, nullptr);
+    if (s != CR_OK) return s;
+    if (ctx->prec == CR_FP64)
+        CR_LAUNCH(ctx, CR_K_OTHER, to_params_kernel<double><<<(P + 255) / 256, 256, 0, ctx->stream>>>(red, P,
+                                                                          (cpx<double>*)grad_params));
+    else
+        CR_LAUNCH(ctx, CR_K_OTHER, to_params_kernel<float><<<(P + 255) / 256, 256, 0, ctx->stream>>>(red, P,
+                                                                         (cpx<float>*)grad_params));
+    return cr_check_launch(ctx, "to_params");
+}

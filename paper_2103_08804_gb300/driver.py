@@ -1,0 +1,149 @@
+"""The Chebyshev recursion driven through the C ABI (Secs. II-III).
+
+Host-side orchestration only: it decides the order of library calls and
+owns the device buffers.  Every arithmetic step runs in libchebrbm kernels,
+and no call inside a moment waits on the host, so a whole moment can be
+enqueued (or captured) in one go.
+
+Order within moment n >= 1 (shared with the oracle):
+  theta <- b + sigma W for the initial RBM_n; n_therm sweeps;
+  n_iter times { sweeps_per_iter sweeps (giving log psi_n, tanh theta);
+                 R = phi_n / psi_n; natural-gradient update;
+                 theta, log psi_n recomputed for the new parameters };
+  sweeps_per_iter sweeps; beta_n = <R> on those samples;
+  mu_n = beta_n < conj(f_q) t~_n / psi > on the fixed samples of |psi|^2,
+  together with the Krylov columns B_n and (H' t_n)/psi.
+RBM_1 starts from psi with a_0 += i pi/2 (exactly proportional to
+S^z_0 psi); RBM_n (n >= 2) starts from RBM_{n-1}.
+"""
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import api
+
+
+@dataclass
+class SeqConfig:
+    Lx: int
+    Ly: int
+    M: int
+    q: tuple
+    n_moments: int
+    n_iter: int
+    shift: float = 1e-3
+    dgamma: float = 0.5
+    J: float = 1.0
+    E0: float = 0.0
+    a: float = 5.0
+    Wp: float = 0.9875
+    n_therm: int = 10
+    sweeps_per_iter: int = 1
+    n_therm_ref: int = 20
+    seed: int = 0
+    seed_ref: int = 1
+    solver: int = api.SOLVE_CG
+    cg_maxit: int = 100
+    cg_tol: float = 1e-6
+    krylov: bool = True
+
+    @property
+    def N(self):
+        return self.Lx * self.Ly
+
+
+class Sequence:
+    """Device state of one Chebyshev sequence (one probe momentum)."""
+
+    def __init__(self, ctx, cfg, psi_params, spins_fit, spins_ref):
+        self.ctx, self.cfg = ctx, cfg
+        dev = torch.device("cuda")
+        cd = ctx.cdtype
+        Nm, P, M = cfg.n_moments, ctx.P, ctx.M
+        self.B = spins_fit.shape[0]
+        self.Bref = spins_ref.shape[0]
+        psi = np.asarray(psi_params, dtype=np.complex128)
+        init1 = psi.copy()
+        init1[0] += 0.5j * np.pi
+        self.params = torch.zeros(Nm, P, dtype=cd, device=dev)
+        self.params[0].copy_(torch.from_numpy(psi).to(cd))
+        self.init1 = torch.from_numpy(init1).to(cd).to(dev)
+        self.spins = torch.as_tensor(spins_fit, dtype=torch.int8).to(dev).contiguous()
+        self.spins_ref = torch.as_tensor(spins_ref, dtype=torch.int8).to(dev).contiguous()
+        self.theta = torch.empty(self.B, M, dtype=cd, device=dev)
+        self.tanh = torch.empty(self.B, M, dtype=cd, device=dev)
+        self.lp = torch.empty(self.B, dtype=cd, device=dev)
+        self.R = torch.empty(self.B, dtype=cd, device=dev)
+        self.theta_ref = torch.empty(self.Bref, M, dtype=cd, device=dev)
+        self.lp_ref = torch.empty(self.Bref, dtype=cd, device=dev)
+        self.betas = torch.zeros(Nm, dtype=torch.complex128, device=dev)
+        self.mu = torch.zeros(Nm, dtype=torch.complex128, device=dev)
+        self.stats = torch.zeros(Nm, max(cfg.n_iter, 1), api.STATS_LEN, dtype=torch.float64,
+                                 device=dev)
+        if cfg.krylov:
+            self.Bmat = torch.zeros(Nm, self.Bref, dtype=cd, device=dev)
+            self.HBmat = torch.zeros(Nm, self.Bref, dtype=cd, device=dev)
+        self.rng = api.Philox(cfg.seed, 0)
+        self.rng_ref = api.Philox(cfg.seed_ref, 0)
+        self.hprime = (cfg.E0, cfg.a, cfg.Wp)
+        self.n_done = 0
+
+    def state(self, n):
+        return self.ctx.state(self.params[n], probe=(n == 0), q=self.cfg.q)
+
+    def start(self):
+        """Sample |psi|^2 once and record mu_0 (beta_0 = 1)."""
+        c, cfg = self.ctx, self.cfg
+        self.betas[0] = 1.0
+        c.rbm_logpsi(self.params[0], self.spins_ref, self.theta_ref, self.lp_ref)
+        c.mc_sweep(self.params[0], self.spins_ref, self.theta_ref, cfg.n_therm_ref, self.rng_ref,
+                   logpsi_out=self.lp_ref)
+        self._moment(0)
+        self.n_done = 1
+
+    def _moment(self, n):
+        c, cfg = self.ctx, self.cfg
+        kw = {}
+        if cfg.krylov:
+            kw = dict(hprime=self.hprime, Bcol=self.Bmat[n], HBcol=self.HBmat[n])
+        c.cheb_moment(self.state(n), self.betas[n:n + 1], cfg.q, self.spins_ref, self.lp_ref,
+                      mu_out=self.mu[n:n + 1], **kw)
+
+    def _target(self, n, mean_out=None):
+        c, cfg = self.ctx, self.cfg
+        prev2 = self.state(n - 2) if n >= 2 else None
+        b2 = self.betas[n - 2:n - 1] if n >= 2 else None
+        c.cheb_local_target(n, self.state(n - 1), prev2, self.betas[n - 1:n], b2, cfg.E0, cfg.a,
+                            cfg.Wp, self.spins, self.lp, self.R, mean_out=mean_out)
+
+    def fit(self, n):
+        """Projection step n: fit RBM_n, then beta_n and mu_n."""
+        c, cfg = self.ctx, self.cfg
+        pn = self.params[n]
+        pn.copy_(self.init1 if n == 1 else self.params[n - 1])
+        c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
+        if cfg.n_therm:
+            c.mc_sweep(pn, self.spins, self.theta, cfg.n_therm, self.rng, logpsi_out=self.lp,
+                       tanh_out=self.tanh)
+        for it in range(cfg.n_iter):
+            c.mc_sweep(pn, self.spins, self.theta, cfg.sweeps_per_iter, self.rng,
+                       logpsi_out=self.lp, tanh_out=self.tanh)
+            self._target(n)
+            c.sr_step(pn, self.spins, self.tanh, self.R, cfg.dgamma, cfg.shift, solver=cfg.solver,
+                      cg_maxit=cfg.cg_maxit, cg_tol=cfg.cg_tol, stats_out=self.stats[n, it])
+            c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
+        c.mc_sweep(pn, self.spins, self.theta, cfg.sweeps_per_iter, self.rng, logpsi_out=self.lp,
+                   tanh_out=self.tanh)
+        self._target(n, mean_out=self.betas[n:n + 1])
+        self._moment(n)
+        self.n_done = n + 1
+
+    def run(self, n_moments=None):
+        nm = self.cfg.n_moments if n_moments is None else n_moments
+        if self.n_done == 0:
+            self.start()
+        for n in range(self.n_done, nm):
+            self.fit(n)
+        return self
