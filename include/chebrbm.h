@@ -134,6 +134,7 @@ typedef struct {
     int solver;             /* CR_SOLVE_CHOLESKY or CR_SOLVE_CG */
     int cg_maxit;           /* CG iteration limit (CG only) */
     double cg_tol;          /* CG stops when |r| <= cg_tol |F| */
+    int cg_precond;         /* 0: plain CG; 1: Jacobi preconditioner diag(S) + shift */
 } cr_sr_opts;
 
 /* ---------------------------------------------------------------- context */

@@ -52,6 +52,10 @@ class Config:
     n_therm_ref: int = 20
     seed: int = 0
     seed_ref: int = 1
+    solver: str = "cholesky"
+    cg_maxit: int = 100
+    cg_tol: float = 1e-6
+    jacobi: bool = False
 
     @property
     def N(self):
@@ -70,6 +74,7 @@ class Result:
     spins_ref: np.ndarray = None
     counter_fit: int = 0
     counter_ref: int = 0
+    samples: dict = field(default_factory=dict)  # n -> [spins of each iteration, beta spins]
 
 
 def initial_params(psi_params, prev_params, n):
@@ -96,8 +101,11 @@ def _moment_columns(cfg, state, beta, spins_ref, lp_ref):
     return Bn, HBn
 
 
-def run_sampled(cfg, psi_params, spins_fit0, spins_ref0, n_moments=None):
-    """The full sampled recursion with the Philox streams of oracle.philox."""
+def run_sampled(cfg, psi_params, spins_fit0, spins_ref0, n_moments=None, record=False):
+    """The full sampled recursion with the Philox streams of oracle.philox.
+
+    record: keep the walker configurations every estimator was taken on
+    (res.samples[n]), so another implementation can replay them."""
     N, M = cfg.N, cfg.M
     bl = lattice.bonds(cfg.Lx, cfg.Ly)
     nm = cfg.n_moments if n_moments is None else n_moments
@@ -120,16 +128,22 @@ def run_sampled(cfg, psi_params, spins_fit0, spins_ref0, n_moments=None):
         g_n = []
         if cfg.n_therm:
             spins, _, ctr = sampler.mc_sweep(params, N, M, bl, spins, cfg.n_therm, cfg.seed, ctr)
+        rec = res.samples.setdefault(n, []) if record else None
         for _ in range(cfg.n_iter):
             spins, _, ctr = sampler.mc_sweep(params, N, M, bl, spins, cfg.sweeps_per_iter,
                                              cfg.seed, ctr)
+            if record:
+                rec.append(spins.copy())
             lp = logpsi(params, N, M, spins)
             R = _target(cfg, n, res, spins, lp)
             O = logderiv(params, N, M, spins)
-            params, info = sr.sr_step(params, O, R, cfg.shift, cfg.dgamma)
+            params, info = sr.sr_step(params, O, R, cfg.shift, cfg.dgamma, solver=cfg.solver,
+                                      cg_maxit=cfg.cg_maxit, cg_tol=cfg.cg_tol, jacobi=cfg.jacobi)
             g_n.append(info["gamma"])
         spins, _, ctr = sampler.mc_sweep(params, N, M, bl, spins, cfg.sweeps_per_iter,
                                          cfg.seed, ctr)
+        if record:
+            rec.append(spins.copy())
         lp = logpsi(params, N, M, spins)
         beta = np.mean(_target(cfg, n, res, spins, lp))
         state = State(params)
@@ -169,7 +183,9 @@ def run_enumerated(cfg, psi_params, n_moments=None):
             lp, w = weights(params)
             R = _target(cfg, n, res, basis, lp)
             O = logderiv(params, N, M, basis)
-            params, info = sr.sr_step(params, O, R, cfg.shift, cfg.dgamma, weights=w)
+            params, info = sr.sr_step(params, O, R, cfg.shift, cfg.dgamma, weights=w,
+                                      solver=cfg.solver, cg_maxit=cfg.cg_maxit,
+                                      cg_tol=cfg.cg_tol, jacobi=cfg.jacobi)
             g_n.append(info["gamma"])
         lp, w = weights(params)
         beta = np.sum(w * _target(cfg, n, res, basis, lp))

@@ -13,7 +13,8 @@ alpha <- alpha + dalpha.  Readings of points the paper leaves open:
   * the argument of the arccos is clamped to <= 1 (sampling noise can push
     it above), and gamma cot gamma is taken as 1 when gamma < 1e-8;
   * the shifted system is solved by Cholesky (S + lambda I is Hermitian
-    positive definite for lambda > 0).
+    positive definite for lambda > 0), or by conjugate gradients, plain or
+    with the Jacobi preconditioner diag(S) + lambda, from x = 0.
 """
 
 import numpy as np
@@ -72,12 +73,48 @@ def shifted_solve(S, F, shift):
     return scipy.linalg.cho_solve(c, F)
 
 
-def sr_step(params, O, R, shift, dgamma, weights=None):
-    """One natural-gradient update.  Returns (new params, info dict)."""
+def cg_solve(S, F, shift, maxit, tol, jacobi=False):
+    """(S + shift I) x = F by conjugate gradients from x = 0 (Hestenes and
+    Stiefel 1952), optionally with the Jacobi preconditioner diag(S) + shift.
+    Stops when |r| <= tol |F| or after maxit iterations.  Returns (x, iterations)."""
+    A = S + shift * np.eye(S.shape[0])
+    d = np.real(np.diag(A)) if jacobi else np.ones(S.shape[0])
+    x = np.zeros_like(F)
+    r = F.copy()
+    z = r / d
+    p = z.copy()
+    rz = np.vdot(r, z).real
+    f2 = np.vdot(F, F).real
+    it = 0
+    if f2 == 0.0:
+        return x, 0
+    while it < maxit:
+        Ap = A @ p
+        alpha = rz / np.vdot(p, Ap).real
+        x = x + alpha * p
+        r = r - alpha * Ap
+        it += 1
+        if np.vdot(r, r).real <= tol * tol * f2:
+            break
+        z = r / d
+        rz_new = np.vdot(r, z).real
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it
+
+
+def sr_step(params, O, R, shift, dgamma, weights=None, solver="cholesky", cg_maxit=100,
+            cg_tol=1e-6, jacobi=False):
+    """One natural-gradient update.  Returns (new params, info dict).
+
+    solver "cholesky": direct solve; "cg": cg_solve with the given options."""
     est = estimators(O, R, weights)
     F, gamma = force(est, dgamma)
     S = qgt(est)
-    delta = shifted_solve(S, F, shift)
+    if solver == "cholesky":
+        delta = shifted_solve(S, F, shift)
+    else:
+        delta, _ = cg_solve(S, F, shift, cg_maxit, cg_tol, jacobi)
     info = {"gamma": gamma, "mR": est["mR"], "mRR": est["mRR"], "F": F, "S": S,
             "delta": delta, "Obar": est["Obar"], "OR": est["OR"]}
     return np.asarray(params, dtype=np.complex128) + delta, info

@@ -51,7 +51,7 @@ class Target(ctypes.Structure):
 class SROpts(ctypes.Structure):
     _fields_ = [("dgamma", ctypes.c_double), ("shift", ctypes.c_double),
                 ("solver", ctypes.c_int), ("cg_maxit", ctypes.c_int),
-                ("cg_tol", ctypes.c_double)]
+                ("cg_tol", ctypes.c_double), ("cg_precond", ctypes.c_int)]
 
 
 _lib = None
@@ -266,7 +266,7 @@ class Context:
         return grad_params
 
     def sr_step(self, params, spins, tanh_theta, R, dgamma, shift, solver=SOLVE_CG, cg_maxit=100,
-                cg_tol=1e-6, stats_out=None):
+                cg_tol=1e-6, stats_out=None, jacobi=False):
         B = self._spins(spins)
         self._c(params, (self.P,), "params")
         self._c(tanh_theta, (B, self.M), "tanh_theta")
@@ -274,7 +274,7 @@ class Context:
         if stats_out is not None and not (stats_out.dtype == torch.float64 and stats_out.is_cuda
                                           and stats_out.numel() >= STATS_LEN):
             raise ValueError("stats_out: need a CUDA float64 tensor of 8 entries")
-        o = SROpts(dgamma, shift, solver, cg_maxit, cg_tol)
+        o = SROpts(dgamma, shift, solver, cg_maxit, cg_tol, 1 if jacobi else 0)
         self._check(self.lib.sr_step(self.h, _ptr(params), _ptr(spins), _ptr(tanh_theta), _ptr(R),
                                      B, ctypes.byref(o), _ptr(stats_out)), "sr_step")
 

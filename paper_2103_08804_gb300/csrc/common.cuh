@@ -176,10 +176,10 @@ struct cr_ctx {
     void* theta_tmp;         // [maxB][M]
     void* lp_tmp;            // [2][maxB]
     void* u_tmp;             // [maxB]
-    double* partial;         // [n_chunks][P + 2] complex128
-    double* red;             // [3][P + 2] complex128 reduced sums
+    double* partial;         // [n_chunks][P + 2 + M] complex128
+    double* red;             // [3][P + 2 + M] complex128 reduced sums
     double* F;               // [P] complex128
-    double* cg;              // x, r, p, Ap: [4][P] complex128
+    double* cg;              // x, r, p, Ap, diag: [5][P] complex128
     void* p_lo;              // [P] context precision
     double* scal;            // scalars [64]
     double* S;               // [P][P] complex128 (explicit S only)

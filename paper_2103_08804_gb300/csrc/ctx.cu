@@ -140,10 +140,10 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
     ALLOC(c->theta_tmp, B * M * cs);
     ALLOC(c->lp_tmp, 2 * B * cs);
     ALLOC(c->u_tmp, B * cs);
-    ALLOC(c->partial, (size_t)c->n_chunks * (P + 2) * 16);
-    ALLOC(c->red, 3 * (P + 2) * 16);
+    ALLOC(c->partial, (size_t)c->n_chunks * (P + 2 + M) * 16);
+    ALLOC(c->red, 3 * (P + 2 + M) * 16);
     ALLOC(c->F, P * 16);
-    ALLOC(c->cg, 4 * P * 16);
+    ALLOC(c->cg, 5 * P * 16);
     ALLOC(c->p_lo, P * cs);
     ALLOC(c->scal, 64 * sizeof(double));
     if (flags & CR_CTX_EXPLICIT_S) {

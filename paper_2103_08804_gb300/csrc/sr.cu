@@ -19,9 +19,11 @@ cr_status logderiv_impl(cr_ctx* ctx, const int8_t* spins, const void* theta, int
 //
 // partial[c][k] = sum over walker chunk c of op(O_k(s)) g_s, k < P, with
 // op = conj or identity, g_s = 1 when g is null; partial[c][P] = sum g_s,
-// partial[c][P+1] = sum |g_s|^2.  Grid (chunk, i-tile): thread t owns hidden
-// units j = t + 128 k and the IT visible units of its tile for O_W; CTAs of
-// tile 0 also produce the a, b and scalar sums.
+// partial[c][P+1] = sum |g_s|^2; the identity pass (the means Obar) also
+// writes partial[c][P+2+j] = sum |T_j(s)|^2, the diagonal of <O* O>.  Rows
+// are P + 2 + M long.  Grid (chunk, i-tile): thread t owns hidden units
+// j = t + 128 k and the IT visible units of its tile for O_W; CTAs of tile
+// 0 also produce the a, b and scalar sums.
 template <typename R, int JPT, int IT, bool CONJ>
 __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__ spins,
                                                       const cpx<R>* __restrict__ T,
@@ -36,9 +38,11 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
     const int c = blockIdx.x, i0 = blockIdx.y * IT, t = threadIdx.x;
     const int s0 = c * chunk, s1 = min(B, s0 + chunk);
     cpx<R> accW[IT][JPT], accb[JPT];
+    R acct[JPT];
 #pragma unroll
     for (int k = 0; k < JPT; ++k) {
         accb[k] = {R(0), R(0)};
+        acct[k] = R(0);
 #pragma unroll
         for (int ii = 0; ii < IT; ++ii) accW[ii][k] = {R(0), R(0)};
     }
@@ -64,6 +68,7 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
                 int j = t + 128 * k;
                 if (j < M) {
                     cpx<R> tv = T[(size_t)s * M + j];
+                    if (!CONJ) acct[k] += abs2(tv);
                     if (CONJ) tv = conj(tv);
                     cpx<R> y = tv * gq;
                     accb[k] = accb[k] + y;
@@ -82,7 +87,7 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
             }
         }
     }
-    cpx<double>* out = (cpx<double>*)partial + (size_t)c * (P + 2);
+    cpx<double>* out = (cpx<double>*)partial + (size_t)c * (P + 2 + M);
 #pragma unroll
     for (int k = 0; k < JPT; ++k) {
         int j = t + 128 * k;
@@ -90,7 +95,10 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
 #pragma unroll
             for (int ii = 0; ii < IT; ++ii)
                 if (i0 + ii < N) out[N + M + (size_t)(i0 + ii) * M + j] = ccast<double>(accW[ii][k]);
-            if (blockIdx.y == 0) out[N + j] = ccast<double>(accb[k]);
+            if (blockIdx.y == 0) {
+                out[N + j] = ccast<double>(accb[k]);
+                if (!CONJ) out[P + 2 + j] = {(double)acct[k], 0.0};
+            }
         }
     }
     if (t < IT && i0 + t < N) out[i0 + t] = ccast<double>(acca);
@@ -100,15 +108,16 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
     }
 }
 
-// red[k] = sum over chunks of partial[c][k], in chunk order.
+// red[k] = sum over chunks of partial[c][k] (k < len, rows `stride` long), in chunk order.
 __global__ void combine_kernel(const double* __restrict__ partial, int n_chunks, int len,
-                               double* __restrict__ red, const double* __restrict__ skip) {
+                               int stride, double* __restrict__ red,
+                               const double* __restrict__ skip) {
     if (skip && *skip != 0.0) return;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= len) return;
     const cpx<double>* p = (const cpx<double>*)partial;
     cpx<double> s = {0.0, 0.0};
-    for (int c = 0; c < n_chunks; ++c) s = s + p[(size_t)c * len + k];
+    for (int c = 0; c < n_chunks; ++c) s = s + p[(size_t)c * stride + k];
     ((cpx<double>*)red)[k] = s;
 }
 
@@ -133,8 +142,9 @@ static cr_status oreduce_t(cr_ctx* c, const int8_t* spins, const void* T, const 
 #undef LAUNCH
     cr_status s = cr_check_launch(c, "oreduce_kernel");
     if (s != CR_OK) return s;
-    CR_LAUNCH(c, CR_K_OTHER, combine_kernel<<<(P + 2 + 255) / 256, 256, 0, c->stream>>>(c->partial, nch, P + 2, red_out,
-                                                                skip));
+    const int len = CONJ ? P + 2 : P + 2 + M;
+    CR_LAUNCH(c, CR_K_OTHER, combine_kernel<<<(len + 255) / 256, 256, 0, c->stream>>>(
+                                 c->partial, nch, len, P + 2 + M, red_out, skip));
     return cr_check_launch(c, "combine_kernel");
 }
 
@@ -303,41 +313,12 @@ __global__ void __launch_bounds__(1024) chol_solve_kernel(double* __restrict__ S
 // ------------------------------------------------------------------- CG
 //
 // Matrix-free S v = (O^dag (O v) - conj(Obar) sum_s (O v)_s) / B, using
-// sum_s (O_s - Obar) = 0.  Vectors x, r, p, Ap and all scalars in float64;
-// the O-products run in the context precision.  scal: [0] r.r, [1] F.F,
-// [2] done flag, [3] iterations.
-
-template <typename R>
-__global__ void __launch_bounds__(1024) cg_init_kernel(const double* __restrict__ F_, int P,
-                                                       double* __restrict__ cg_,
-                                                       cpx<R>* __restrict__ p_lo,
-                                                       double* __restrict__ scal) {
-    const cpx<double>* F = (const cpx<double>*)F_;
-    cpx<double>* x = (cpx<double>*)cg_;
-    cpx<double>* r = x + P;
-    cpx<double>* p = x + 2 * P;
-    __shared__ double red[32];
-    double rr = 0.0;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
-        cpx<double> f = F[k];
-        x[k] = {0.0, 0.0};
-        r[k] = f;
-        p[k] = f;
-        p_lo[k] = ccast<R>(f);
-        rr += abs2(f);
-    }
-    rr = warp_sum(rr);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rr;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        scal[0] = t;
-        scal[1] = t;
-        scal[2] = t == 0.0 ? 1.0 : 0.0;
-        scal[3] = 0.0;
-    }
-}
+// sum_s (O_s - Obar) = 0.  Conjugate gradients from x = 0 (Hestenes and
+// Stiefel), optionally preconditioned with d = diag(S) + shift, where
+// S_kk = <|O_k|^2> - |Obar_k|^2 with |O_a|^2 = 1 and |O_b|^2 = |O_W|^2 =
+// |T_j|^2.  Vectors x, r, p, Ap, d and all scalars in float64; the
+// O-products run in the context precision.  scal: [0] r.z, [1] F.F,
+// [2] done flag, [3] iterations, [4] r.r.
 
 __device__ double block_sum(double v, double* red) {
     v = warp_sum(v);
@@ -347,6 +328,49 @@ __device__ double block_sum(double v, double* red) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
     return t;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) cg_init_kernel(const double* __restrict__ F_,
+                                                       const double* __restrict__ redO_, int N,
+                                                       int M, int P, int B, double shift,
+                                                       int precond, double* __restrict__ cg_,
+                                                       cpx<R>* __restrict__ p_lo,
+                                                       double* __restrict__ scal) {
+    __shared__ double red[32];
+    const cpx<double>* F = (const cpx<double>*)F_;
+    const cpx<double>* sO = (const cpx<double>*)redO_;
+    cpx<double>* x = (cpx<double>*)cg_;
+    cpx<double>* r = x + P;
+    cpx<double>* p = x + 2 * P;
+    cpx<double>* dg = x + 4 * P;
+    const double inv = 1.0 / B;
+    double ff = 0.0, rz = 0.0;
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        double d = 1.0;
+        if (precond) {
+            double o2 = k < N ? 1.0 : inv * sO[P + 2 + (k < N + M ? k - N : (k - N - M) % M)].x;
+            d = o2 - abs2(inv * sO[k]) + shift;
+        }
+        cpx<double> f = F[k];
+        cpx<double> z = (1.0 / d) * f;
+        x[k] = {0.0, 0.0};
+        r[k] = f;
+        p[k] = z;
+        dg[k] = {d, 0.0};
+        p_lo[k] = ccast<R>(z);
+        ff += abs2(f);
+        rz += cmulc(f, z).x;
+    }
+    ff = block_sum(ff, red);
+    rz = block_sum(rz, red);
+    if (threadIdx.x == 0) {
+        scal[0] = rz;
+        scal[1] = ff;
+        scal[2] = ff == 0.0 ? 1.0 : 0.0;
+        scal[3] = 0.0;
+        scal[4] = ff;
+    }
 }
 
 // One CG step after red = [sum conj(O) u | sum u | .] for u = O p.
@@ -365,6 +389,7 @@ __global__ void __launch_bounds__(1024) cg_step_kernel(const double* __restrict_
     cpx<double>* r = x + P;
     cpx<double>* p = x + 2 * P;
     cpx<double>* Ap = x + 3 * P;
+    const cpx<double>* dg = x + 4 * P;
     const double inv = 1.0 / B;
     const cpx<double> mu = inv * sOu[P];
     double pap = 0.0;
@@ -374,8 +399,8 @@ __global__ void __launch_bounds__(1024) cg_step_kernel(const double* __restrict_
         pap += cmulc(p[k], a).x;
     }
     pap = block_sum(pap, red);
-    const double rr = scal[0];
-    const double alpha = rr / pap;
+    const double rz = scal[0];
+    const double alpha = rz / pap;
     double rn = 0.0;
     for (int k = threadIdx.x; k < P; k += blockDim.x) {
         x[k] = x[k] + alpha * p[k];
@@ -384,18 +409,23 @@ __global__ void __launch_bounds__(1024) cg_step_kernel(const double* __restrict_
         rn += abs2(rk);
     }
     rn = block_sum(rn, red);
-    const double beta = rn / rr;
     const bool done = !(rn > tol * tol * scal[1]);
-    if (!done)
+    double rzn = 0.0;
+    if (!done) {
+        for (int k = threadIdx.x; k < P; k += blockDim.x) rzn += (1.0 / dg[k].x) * abs2(r[k]);
+        rzn = block_sum(rzn, red);
+        const double beta = rzn / rz;
         for (int k = threadIdx.x; k < P; k += blockDim.x) {
-            cpx<double> pk = r[k] + beta * p[k];
+            cpx<double> pk = (1.0 / dg[k].x) * r[k] + beta * p[k];
             p[k] = pk;
             p_lo[k] = ccast<R>(pk);
         }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        scal[0] = rn;
+        scal[0] = rzn;
         scal[3] += 1.0;
+        scal[4] = rn;
         if (done) scal[2] = 1.0;
     }
 }
@@ -414,7 +444,7 @@ __global__ void apply_update_kernel(cpx<R>* __restrict__ prm, const double* __re
     }
     if (k == 0 && stats) {
         stats[5] = cg ? scal[3] : 0.0;
-        stats[6] = cg ? (scal[1] > 0 ? sqrt(scal[0] / scal[1]) : 0.0) : 0.0;
+        stats[6] = cg ? (scal[1] > 0 ? sqrt(scal[4] / scal[1]) : 0.0) : 0.0;
         stats[7] = sqrt(scal[1]);
     }
 }
@@ -433,8 +463,8 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
                            const void* Rv, int B, const cr_sr_opts* o, double* stats) {
     const int P = c->P;
     double* redR = c->red;
-    double* redO = c->red + 2 * (P + 2);
-    double* redU = c->red + 4 * (P + 2);
+    double* redO = c->red + 2 * (P + 2 + c->M);
+    double* redU = c->red + 4 * (P + 2 + c->M);
     cr_status s = oreduce(c, true, spins, T, Rv, B, redR, nullptr);
     if (s != CR_OK) return s;
     s = oreduce(c, false, spins, T, nullptr, B, redO, nullptr);
@@ -454,7 +484,9 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
         CR_LAUNCH(c, CR_K_OTHER, fnorm_kernel<<<1, 1024, 0, c->stream>>>(c->F, P, c->scal));
         if ((s = cr_check_launch(c, "cholesky path")) != CR_OK) return s;
     } else {
-        CR_LAUNCH(c, CR_K_OTHER, cg_init_kernel<R><<<1, 1024, 0, c->stream>>>(c->F, P, c->cg, (cpx<R>*)c->p_lo, c->scal));
+        CR_LAUNCH(c, CR_K_OTHER, cg_init_kernel<R><<<1, 1024, 0, c->stream>>>(
+                                     c->F, redO, c->N, c->M, P, B, o->shift, o->cg_precond,
+                                     c->cg, (cpx<R>*)c->p_lo, c->scal));
         if ((s = cr_check_launch(c, "cg_init")) != CR_OK) return s;
         const double* done = c->scal + 2;
         for (int it = 0; it < o->cg_maxit; ++it) {
@@ -484,7 +516,8 @@ extern "C" cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, con
                  "sr_step: unknown solver");
     CR_CHECK_ARG(opts->solver != CR_SOLVE_CHOLESKY || (ctx->flags & CR_CTX_EXPLICIT_S),
                  "sr_step: Cholesky needs a context created with CR_CTX_EXPLICIT_S");
-    CR_CHECK_ARG(opts->solver != CR_SOLVE_CG || (opts->cg_maxit >= 1 && opts->cg_tol >= 0.0),
+    CR_CHECK_ARG(opts->solver != CR_SOLVE_CG || (opts->cg_maxit >= 1 && opts->cg_tol >= 0.0 &&
+                                                 (opts->cg_precond == 0 || opts->cg_precond == 1)),
                  "sr_step: bad CG options");
     return ctx->prec == CR_FP64
                ? sr_step_t<double>(ctx, params, spins, tanh_theta, R, B, opts, stats_out)

@@ -47,6 +47,7 @@ class SeqConfig:
     solver: int = api.SOLVE_CG
     cg_maxit: int = 100
     cg_tol: float = 1e-6
+    jacobi: bool = False
     krylov: bool = True
 
     @property
@@ -93,13 +94,17 @@ class Sequence:
     def state(self, n):
         return self.ctx.state(self.params[n], probe=(n == 0), q=self.cfg.q)
 
-    def start(self):
-        """Sample |psi|^2 once and record mu_0 (beta_0 = 1)."""
+    def start(self, replay_ref=None):
+        """Sample |psi|^2 once (or take the recorded samples replay_ref) and
+        record mu_0 (beta_0 = 1)."""
         c, cfg = self.ctx, self.cfg
         self.betas[0] = 1.0
+        if replay_ref is not None:
+            self.spins_ref.copy_(replay_ref)
         c.rbm_logpsi(self.params[0], self.spins_ref, self.theta_ref, self.lp_ref)
-        c.mc_sweep(self.params[0], self.spins_ref, self.theta_ref, cfg.n_therm_ref, self.rng_ref,
-                   logpsi_out=self.lp_ref)
+        if replay_ref is None:
+            c.mc_sweep(self.params[0], self.spins_ref, self.theta_ref, cfg.n_therm_ref,
+                       self.rng_ref, logpsi_out=self.lp_ref)
         self._moment(0)
         self.n_done = 1
 
@@ -118,24 +123,43 @@ class Sequence:
         c.cheb_local_target(n, self.state(n - 1), prev2, self.betas[n - 1:n], b2, cfg.E0, cfg.a,
                             cfg.Wp, self.spins, self.lp, self.R, mean_out=mean_out)
 
-    def fit(self, n):
-        """Projection step n: fit RBM_n, then beta_n and mu_n."""
+    def _samples(self, pn, n_sweeps, replay):
+        """Fresh samples of |psi_n|^2: Metropolis sweeps, or, when replaying,
+        the next recorded configuration set (then theta, log psi and tanh theta
+        are evaluated on it)."""
+        c = self.ctx
+        if replay is None:
+            c.mc_sweep(pn, self.spins, self.theta, n_sweeps, self.rng, logpsi_out=self.lp,
+                       tanh_out=self.tanh)
+        else:
+            self.spins.copy_(next(replay))
+            c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
+            c.logderiv(pn, self.spins, self.theta, tanh_out=self.tanh)
+
+    def fit(self, n, replay=None):
+        """Projection step n: fit RBM_n, then beta_n and mu_n.
+
+        replay: optional iterable of walker configurations (device int8
+        [B, N]) to use, in order, instead of the sampler: one per iteration
+        and one for beta_n (the recorded samples of another run)."""
         c, cfg = self.ctx, self.cfg
+        replay = iter(replay) if replay is not None else None
         pn = self.params[n]
         pn.copy_(self.init1 if n == 1 else self.params[n - 1])
-        c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
-        if cfg.n_therm:
-            c.mc_sweep(pn, self.spins, self.theta, cfg.n_therm, self.rng, logpsi_out=self.lp,
-                       tanh_out=self.tanh)
+        if replay is None:
+            c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
+            if cfg.n_therm:
+                c.mc_sweep(pn, self.spins, self.theta, cfg.n_therm, self.rng, logpsi_out=self.lp,
+                           tanh_out=self.tanh)
         for it in range(cfg.n_iter):
-            c.mc_sweep(pn, self.spins, self.theta, cfg.sweeps_per_iter, self.rng,
-                       logpsi_out=self.lp, tanh_out=self.tanh)
+            self._samples(pn, cfg.sweeps_per_iter, replay)
             self._target(n)
             c.sr_step(pn, self.spins, self.tanh, self.R, cfg.dgamma, cfg.shift, solver=cfg.solver,
-                      cg_maxit=cfg.cg_maxit, cg_tol=cfg.cg_tol, stats_out=self.stats[n, it])
-            c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
-        c.mc_sweep(pn, self.spins, self.theta, cfg.sweeps_per_iter, self.rng, logpsi_out=self.lp,
-                   tanh_out=self.tanh)
+                      cg_maxit=cfg.cg_maxit, cg_tol=cfg.cg_tol, stats_out=self.stats[n, it],
+                      jacobi=cfg.jacobi)
+            if replay is None:
+                c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
+        self._samples(pn, cfg.sweeps_per_iter, replay)
         self._target(n, mean_out=self.betas[n:n + 1])
         self._moment(n)
         self.n_done = n + 1

@@ -76,6 +76,27 @@ def test_shifted_solve_residual():
     assert np.linalg.norm((S + 1e-3 * np.eye(20)) @ x - F) < 1e-10 * np.linalg.norm(F)
 
 
+@pytest.mark.parametrize("jacobi", [False, True])
+def test_cg_reaches_the_direct_solution(jacobi):
+    # conjugate gradients on an n x n SPD system terminate in at most n steps in
+    # exact arithmetic; with a badly scaled diagonal the Jacobi variant needs fewer
+    rng = np.random.default_rng(40)
+    O = rng.standard_normal((400, 30)) + 1j * rng.standard_normal((400, 30))
+    O[:, :10] *= 30.0
+    est = sr.estimators(O, rng.standard_normal(400) + 0j)
+    S = sr.qgt(est)
+    F = rng.standard_normal(30) + 1j * rng.standard_normal(30)
+    x_direct = sr.shifted_solve(S, F, 1e-2)
+    x, it = sr.cg_solve(S, F, 1e-2, 200, 1e-12, jacobi)
+    assert np.linalg.norm(x - x_direct) < 1e-9 * np.linalg.norm(x_direct)
+    assert it <= 120
+    _, it1 = sr.cg_solve(S, F, 1e-2, 1, 0.0, jacobi)
+    assert it1 == 1
+    if jacobi:
+        _, it_plain = sr.cg_solve(S, F, 1e-2, 200, 1e-12, False)
+        assert it < it_plain
+
+
 def test_natural_gradient_fit_converges_on_representable_target():
     # phi = i sigma_0 psi0 is exactly the RBM psi0 with a_0 += i pi / 2.
     N, M = 8, 8
