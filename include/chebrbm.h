@@ -227,6 +227,31 @@ cr_status logpsi_backward(cr_ctx* ctx, const cr_state* state, const int8_t* spin
                           const void* tanh_theta, int B, const void* grad_logpsi,
                           void* grad_params);
 
+/* logpsi_backward without any allocation.  The paper has no counterpart:
+   this entry point exists for callers that cannot allocate device memory
+   themselves -- code inside a framework whose caching allocator owns the
+   device's memory, plugins or services held to a fixed footprint, or callers
+   that must avoid the device-wide synchronisation a cudaFree brings -- and
+   so cannot create a context.  It computes the same
+   grad_params[k] = sum_s g_s conj(O_k(s)) as logpsi_backward, with no context:
+   N, M and the precision (complex128 for CR_FP64, complex64 otherwise) are
+   arguments, and the work runs on `stream` (a cudaStream_t, NULL = legacy
+   default stream).  Its reduction scratch is a fixed 4 MiB float64 array in
+   the library's device image (held by every GPU that loads the library until
+   the process exits), which bounds the size: N + M + N*M up to about 131,000
+   parameters (2 <= N <= 1024, 1 <= M <= 512); larger sizes return CR_EINVAL.
+   The call allocates nothing and calls no allocating routine.  The first call
+   on each device looks up the scratch array's device address for that device
+   (cudaGetSymbolAddress), so make that first call before any stream capture.
+   All calls share the one array and it keeps the last call's contents (every
+   entry a call reads is written by that call first, so nothing needs
+   clearing); calls whose work overlaps on the GPU race on it, so serialise
+   them (one stream, or events).  errbuf (host, errbuf_len bytes, or NULL)
+   receives the reason for a non-CR_OK status. */
+cr_status logpsi_backward_noalloc(int N, int M, cr_prec prec, const int8_t* spins,
+                                  const void* tanh_theta, int B, const void* grad_logpsi,
+                                  void* grad_params, void* stream, char* errbuf, int errbuf_len);
+
 /* Sec. III natural-gradient update, on samples of |psi|^2:
      gamma = arccos sqrt(min(1, |<R>|^2 / <|R|^2>)),
      F_k   = dgamma * gamma cot gamma * (<O_k* R>/<R> - <O_k*>)   (gamma cot gamma = 1 below 1e-8),

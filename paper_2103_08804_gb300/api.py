@@ -25,7 +25,8 @@ STATUS = {0: "CR_OK", 1: "CR_EINVAL", 2: "CR_ENOMEM", 3: "CR_ECUDA", 4: "CR_ETIM
 SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync_status",
            "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds", "rbm_logpsi", "mc_sweep",
            "cheb_local_target", "logderiv", "logpsi_backward", "sr_step", "cheb_moment",
-           "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times")
+           "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
+           "logpsi_backward_noalloc")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5}
 
 
@@ -90,6 +91,7 @@ def load(path=None):
     lib.cr_n_launches.restype = ctypes.c_longlong
     lib.cr_time_kernel.argtypes = [vp, i, i]
     lib.cr_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
+    lib.logpsi_backward_noalloc.argtypes = [i, i, i, vp, vp, i, vp, vp, vp, ctypes.c_char_p, i]
     for f in SYMBOLS:
         if f not in ("cr_last_error", "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds",
                      "cr_n_launches"):

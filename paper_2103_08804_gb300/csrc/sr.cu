@@ -556,3 +556,121 @@ extern "C" cr_status logpsi_backward(cr_ctx* ctx, const cr_state* st, const int8
                                                                          (cpx<float>*)grad_params));
     return cr_check_launch(ctx, "to_params");
 }
+
+// ------------------------------------- VJP of log psi without allocation
+//
+// For callers that cannot allocate device memory themselves: code running
+// inside a framework whose caching allocator owns the device's memory
+// budget, plugins and services given a fixed footprint, or callers that
+// must not trigger the device-wide synchronisation cudaFree implies.  The
+// reduction scratch of logpsi_backward is a fixed array in the library's
+// own device image instead of context workspace.
+
+// 4 MiB of float64: partial rows [chunks][P + 2 + M] complex128 followed by
+// the reduced row [P + 2] complex128.  Every GPU that loads the library
+// holds it until the process exits.
+#define CR_NOALLOC_SCRATCH_DOUBLES (512 * 1024)
+static __device__ __align__(256) double g_noalloc_scratch[CR_NOALLOC_SCRATCH_DOUBLES];
+
+#define CR_NOALLOC_MAX_DEVICES 64
+static double* g_noalloc_ptr[CR_NOALLOC_MAX_DEVICES];
+
+static void noalloc_err(char* buf, int len, const char* msg) {
+    if (buf && len > 0) {
+        strncpy(buf, msg, (size_t)len - 1);
+        buf[len - 1] = '\0';
+    }
+}
+
+template <typename R>
+static cudaError_t noalloc_backward_t(int N, int M, const int8_t* spins, const void* T, int B,
+                                      const void* g, void* grad, int nch, double* scratch,
+                                      cudaStream_t st) {
+    const int P = N + M + N * M;
+    const int chunk = (B + nch - 1) / nch;
+    const int jpt = (M + 127) / 128;
+    const bool dbl = sizeof(R) == 8;
+    double* red = scratch + (size_t)nch * (P + 2 + M) * 2;
+#define LAUNCH(JPT, IT)                                                                    \
+    oreduce_kernel<R, JPT, IT, true><<<dim3(nch, (N + IT - 1) / IT), 128, 0, st>>>(        \
+        spins, (const cpx<R>*)T, (const cpx<R>*)g, B, N, M, P, chunk, scratch, nullptr)
+    if (jpt == 1) {
+        if (dbl) LAUNCH(1, 8); else LAUNCH(1, 16);
+    } else if (jpt == 2) {
+        if (dbl) LAUNCH(2, 4); else LAUNCH(2, 8);
+    } else {
+        if (dbl) LAUNCH(4, 2); else LAUNCH(4, 4);
+    }
+#undef LAUNCH
+    combine_kernel<<<(P + 2 + 255) / 256, 256, 0, st>>>(scratch, nch, P + 2, P + 2 + M, red,
+                                                         nullptr);
+    to_params_kernel<R><<<(P + 255) / 256, 256, 0, st>>>(red, P, (cpx<R>*)grad);
+    return cudaGetLastError();
+}
+
+extern "C" cr_status logpsi_backward_noalloc(int N, int M, cr_prec prec, const int8_t* spins,
+                                             const void* tanh_theta, int B,
+                                             const void* grad_logpsi, void* grad_params,
+                                             void* stream, char* errbuf, int errbuf_len) {
+    if (N < 2 || N > 1024 || M < 1 || M > 512 || B < 0) {
+        noalloc_err(errbuf, errbuf_len, "logpsi_backward_noalloc: need 2 <= N <= 1024, "
+                                        "1 <= M <= 512, B >= 0");
+        return CR_EINVAL;
+    }
+    if (prec != CR_FP64 && prec != CR_FP32 && prec != CR_MIXED) {
+        noalloc_err(errbuf, errbuf_len, "logpsi_backward_noalloc: unknown precision");
+        return CR_EINVAL;
+    }
+    const long long P = (long long)N + M + (long long)N * M;
+    const long long row = 2 * (P + 2 + M), tail = 2 * (P + 2);
+    long long nch = (CR_NOALLOC_SCRATCH_DOUBLES - tail) / row;
+    if (nch < 1) {
+        noalloc_err(errbuf, errbuf_len, "logpsi_backward_noalloc: N + M + N*M too large for "
+                                        "the 4 MiB scratch (limit about 131000 parameters)");
+        return CR_EINVAL;
+    }
+    if (!grad_params || (B > 0 && (!spins || !tanh_theta || !grad_logpsi))) {
+        noalloc_err(errbuf, errbuf_len, "logpsi_backward_noalloc: null array");
+        return CR_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t rs = prec == CR_FP64 ? 8 : 4;
+    if (B == 0) {
+        cudaError_t e = cudaMemsetAsync(grad_params, 0, (size_t)P * 2 * rs, st);
+        if (e != cudaSuccess) {
+            noalloc_err(errbuf, errbuf_len, cudaGetErrorString(e));
+            return CR_ECUDA;
+        }
+        return CR_OK;
+    }
+    // once per device, with that device current: the device address of the
+    // scratch array (in host code its name is only a host-side stand-in)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= CR_NOALLOC_MAX_DEVICES) {
+        noalloc_err(errbuf, errbuf_len, "logpsi_backward_noalloc: no usable current device");
+        return CR_ECUDA;
+    }
+    double* scratch = __atomic_load_n(&g_noalloc_ptr[dev], __ATOMIC_ACQUIRE);
+    if (!scratch) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            noalloc_err(errbuf, errbuf_len, "logpsi_backward_noalloc: cudaGetSymbolAddress failed");
+            return CR_ECUDA;
+        }
+        scratch = (double*)p;
+        __atomic_store_n(&g_noalloc_ptr[dev], scratch, __ATOMIC_RELEASE);
+    }
+    if (nch > 64) nch = 64;
+    if (nch > B) nch = B;
+    e = prec == CR_FP64 ? noalloc_backward_t<double>(N, M, spins, tanh_theta, B, grad_logpsi,
+                                                     grad_params, (int)nch, scratch, st)
+                        : noalloc_backward_t<float>(N, M, spins, tanh_theta, B, grad_logpsi,
+                                                    grad_params, (int)nch, scratch, st);
+    if (e != cudaSuccess) {
+        noalloc_err(errbuf, errbuf_len, cudaGetErrorString(e));
+        return CR_ECUDA;
+    }
+    return CR_OK;
+}
