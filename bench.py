@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed"])
     ap.add_argument("--cg-maxit", type=int, default=50)
     ap.add_argument("--cg-tol", type=float, default=1e-4)
+    ap.add_argument("--jacobi", action="store_true", help="Jacobi-preconditioned CG")
+    ap.add_argument("--iters", type=int, default=None,
+                    help="natural-gradient iterations per moment (profiling runs only; the "
+                         "workload's own count otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-walkers", type=int, default=2048)
     return ap.parse_args()
@@ -134,10 +138,10 @@ def measured_peaks():
 def make_config(wl, E0, a, args, n_moments, seed):
     from paper_2103_08804_gb300 import api, driver
     return driver.SeqConfig(Lx=wl.Lx, Ly=wl.Ly, M=wl.M, q=wl.q, n_moments=n_moments,
-                            n_iter=wl.iters, shift=wl.shift, dgamma=wl.dgamma, E0=E0, a=a,
+                            n_iter=wl.iters if args.iters is None else args.iters, shift=wl.shift, dgamma=wl.dgamma, E0=E0, a=a,
                             Wp=0.9875, n_therm=2, sweeps_per_iter=1, n_therm_ref=20, seed=seed,
                             seed_ref=seed + 1, solver=api.SOLVE_CG, cg_maxit=args.cg_maxit,
-                            cg_tol=args.cg_tol, krylov=True)
+                            cg_tol=args.cg_tol, jacobi=args.jacobi, krylov=True)
 
 
 def reduce_flops(wl):
@@ -231,8 +235,8 @@ def run_ours(args):
                                "P=8384), 16384 walkers, q=pi/2, 50 natural-gradient iterations "
                                "per moment, matrix-free CG shifted solve",
                    "path": "plain fp32" if prec == api.FP32 else "mixed",
-                   "walkers": wl.walkers, "iters_per_moment": wl.iters,
-                   "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol,
+                   "walkers": wl.walkers, "iters_per_moment": cfg.n_iter,
+                   "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol, "jacobi": args.jacobi,
                    "cg_iters_mean": cg_iters, "l2": "256 MiB buffer written between timed steps",
                    "parallelism": f"replicas x{ws}"},
         "mc_samples_per_s": ws * wl.walkers * sweeps_per_moment / (ms * 1e-3),

@@ -181,6 +181,8 @@ struct cr_ctx {
     double* F;               // [P] complex128
     double* cg;              // x, r, p, Ap, diag: [5][P] complex128
     void* p_lo;              // [P] context precision
+    double* cgpart;          // per-CTA dot products of a CG step: p.Ap [ceil(P/32)],
+                             // r.r and r.z [2][ceil(P/256)]
     double* scal;            // scalars [64]
     double* S;               // [P][P] complex128 (explicit S only)
     void* O_tmp;             // [maxB][P] context precision (explicit S only)

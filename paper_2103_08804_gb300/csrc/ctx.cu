@@ -116,8 +116,10 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
     c->flags = flags;
     c->stream = (cudaStream_t)stream;
     c->kt.kid = -1;
-    c->n_chunks = (max_walkers + 255) / 256;
-    if (c->n_chunks > 64) c->n_chunks = 64;
+    // walker chunks of the reductions: enough CTAs to fill the GPU, each chunk
+    // at least 128 walkers; partial rows cost (P + 2 + M) x 16 bytes each
+    c->n_chunks = (max_walkers + 127) / 128;
+    if (c->n_chunks > 128) c->n_chunks = 128;
     if (c->N > 1024 || c->N % 2) {
         free(c);
         return CR_EINVAL;
@@ -145,6 +147,7 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
     ALLOC(c->F, P * 16);
     ALLOC(c->cg, 5 * P * 16);
     ALLOC(c->p_lo, P * cs);
+    ALLOC(c->cgpart, ((P + 31) / 32 + 2 * ((P + 255) / 256)) * sizeof(double));
     ALLOC(c->scal, 64 * sizeof(double));
     if (flags & CR_CTX_EXPLICIT_S) {
         ALLOC(c->S, P * P * 16);
@@ -171,7 +174,7 @@ extern "C" cr_status cr_destroy(cr_ctx* c) {
     if (!c) return CR_EINVAL;
     kt_free(c);
     void* ptrs[] = {c->d_status, c->d_bonds, c->theta_tmp, c->lp_tmp, c->u_tmp, c->partial,
-                    c->red, c->F, c->cg, c->p_lo, c->scal, c->S, c->O_tmp, c->kry};
+                    c->red, c->F, c->cg, c->p_lo, c->cgpart, c->scal, c->S, c->O_tmp, c->kry};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int s = 0; s < 2; ++s) {

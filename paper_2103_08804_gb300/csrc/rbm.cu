@@ -71,13 +71,13 @@ __global__ void __launch_bounds__(128) theta_kernel(const cpx<R>* __restrict__ p
                                                     const double* __restrict__ skip) {
     if (skip && *skip != 0.0) return;  // converged CG: nothing left to do
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sg = (R*)smem_raw;                       // [WB][N]
+    R* sg = (R*)smem_raw;                       // [N][WB]: the WB signs of site i together
     cpx<R>* red = (cpx<R>*)(sg + WB * N);       // [4][WB]
     const int w0 = blockIdx.x * WB;
     const int t = threadIdx.x;
     for (int e = t; e < WB * N; e += 128) {
         int w = e / N, i = e % N;
-        sg[e] = (w0 + w < B) ? R(spins[(size_t)(w0 + w) * N + i]) : R(0);
+        sg[i * WB + w] = (w0 + w < B) ? R(spins[(size_t)(w0 + w) * N + i]) : R(0);
     }
     __syncthreads();
     const cpx<R>* a = prm;
@@ -91,20 +91,34 @@ __global__ void __launch_bounds__(128) theta_kernel(const cpx<R>* __restrict__ p
 #pragma unroll
         for (int w = 0; w < WB; ++w) acc[w][k] = bj;
     }
+    // W rows are loaded one step ahead so that their latency overlaps the FMAs
+    cpx<R> wnext[JPT];
+#pragma unroll
+    for (int k = 0; k < JPT; ++k) {
+        int j = t + 128 * k;
+        wnext[k] = (j < M && N > 0) ? W[j] : cpx<R>{R(0), R(0)};
+    }
     for (int i = 0; i < N; ++i) {
         cpx<R> wv[JPT];
 #pragma unroll
         for (int k = 0; k < JPT; ++k) {
+            wv[k] = wnext[k];
             int j = t + 128 * k;
-            wv[k] = j < M ? W[(size_t)i * M + j] : cpx<R>{R(0), R(0)};
+            wnext[k] = (j < M && i + 1 < N) ? W[(size_t)(i + 1) * M + j] : cpx<R>{R(0), R(0)};
+        }
+        // WB signs in 16-byte shared loads
+        R sv[WB];
+#pragma unroll
+        for (int w = 0; w < WB; w += 16 / sizeof(R)) {
+            uint4 v = *reinterpret_cast<const uint4*>(sg + i * WB + w);
+            memcpy(&sv[w], &v, 16);
         }
 #pragma unroll
         for (int w = 0; w < WB; ++w) {
-            R s = sg[w * N + i];
 #pragma unroll
             for (int k = 0; k < JPT; ++k) {
-                acc[w][k].x = fma(s, wv[k].x, acc[w][k].x);
-                acc[w][k].y = fma(s, wv[k].y, acc[w][k].y);
+                acc[w][k].x = fma(sv[w], wv[k].x, acc[w][k].x);
+                acc[w][k].y = fma(sv[w], wv[k].y, acc[w][k].y);
             }
         }
     }
@@ -125,7 +139,7 @@ __global__ void __launch_bounds__(128) theta_kernel(const cpx<R>* __restrict__ p
                 }
             }
         }
-        for (int i = t; i < N; i += 128) part[w] = part[w] + sg[w * N + i] * a[i];
+        for (int i = t; i < N; i += 128) part[w] = part[w] + sg[i * WB + w] * a[i];
     }
     const int lane = t & 31, wid = t >> 5;
 #pragma unroll

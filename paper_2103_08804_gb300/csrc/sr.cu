@@ -108,6 +108,130 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
     }
 }
 
+// Register-tiled form of the same reduction (used by the hot path).  Each CTA
+// of 128 threads takes a walker chunk and a tile of 64 visible x 32 hidden
+// units; thread t owns visible units i0 + 4 (t / 8) + {0..3} and hidden units
+// j0 + 4 (t % 8) + {0..3}, so each staged step feeds 32 FMAs from 3 shared
+// loads.  Y_sj = op(T_sj) g_s is formed once per walker while staging, and
+// the next sub-block's T and spins are fetched into registers while the
+// current one is consumed.  Partial rows and their layout are those of
+// oreduce_kernel.
+template <typename R, bool CONJ>
+__global__ void __launch_bounds__(128) oreduce2_kernel(const int8_t* __restrict__ spins,
+                                                       const cpx<R>* __restrict__ T,
+                                                       const cpx<R>* __restrict__ g, int B, int N,
+                                                       int M, int P, int chunk,
+                                                       double* __restrict__ partial,
+                                                       const double* __restrict__ skip) {
+    if (skip && *skip != 0.0) return;
+    constexpr int SUB = 32, TI = 64, TJ = 32, NT = 128;
+    constexpr int SE = SUB * TI / NT, YE = SUB * TJ / NT;   // staged elements per thread
+    __shared__ __align__(16) R sg[SUB][TI];
+    __shared__ __align__(16) cpx<R> ys[SUB][TJ];
+    __shared__ cpx<R> gs[SUB];
+    const int c = blockIdx.x, j0 = blockIdx.y * TJ, i0 = blockIdx.z * TI;
+    const int t = threadIdx.x, ti = 4 * (t >> 3), tj = 4 * (t & 7);
+    const int s0 = c * chunk, s1 = min(B, s0 + chunk);
+    const bool a_cta = blockIdx.y == 0, b_cta = blockIdx.z == 0;
+    cpx<R> acc[4][4], accb[4];
+    R acct[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][k] = {R(0), R(0)};
+        accb[k] = {R(0), R(0)};
+        acct[k] = R(0);
+    }
+    cpx<R> acca = {R(0), R(0)}, accg = {R(0), R(0)};
+    R accgg = R(0);
+    // register prefetch of one sub-block
+    int8_t sp[SE];
+    cpx<R> tp[YE];
+    auto fetch = [&](int sb) {
+#pragma unroll
+        for (int u = 0; u < SE; ++u) {
+            const int e = t + u * NT, w = e / TI, i = e % TI, s = sb + w;
+            sp[u] = (s < s1 && i0 + i < N) ? spins[(size_t)s * N + i0 + i] : (int8_t)0;
+        }
+#pragma unroll
+        for (int u = 0; u < YE; ++u) {
+            const int e = t + u * NT, w = e / TJ, j = e % TJ, s = sb + w;
+            tp[u] = (s < s1 && j0 + j < M) ? T[(size_t)s * M + j0 + j] : cpx<R>{R(0), R(0)};
+        }
+    };
+    if (s0 < s1) fetch(s0);
+    for (int sb = s0; sb < s1; sb += SUB) {
+        __syncthreads();
+        if (t < SUB) {
+            const int s = sb + t;
+            gs[t] = s < s1 ? (g ? g[s] : cpx<R>{R(1), R(0)}) : cpx<R>{R(0), R(0)};
+        }
+#pragma unroll
+        for (int u = 0; u < SE; ++u) {
+            const int e = t + u * NT;
+            sg[e / TI][e % TI] = R(sp[u]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < YE; ++u) {
+            const int e = t + u * NT, w = e / TJ;
+            cpx<R> tv = tp[u];
+            if (CONJ) tv = conj(tv);
+            ys[w][e % TJ] = tv * gs[w];
+        }
+        if (sb + SUB < s1) fetch(sb + SUB);
+        __syncthreads();
+        const int ns = min(SUB, s1 - sb);
+        for (int q = 0; q < ns; ++q) {
+            R sv[4];
+            cpx<R> y[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) sv[a] = sg[q][ti + a];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) y[k] = ys[q][tj + k];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    acc[a][k].x = fma(sv[a], y[k].x, acc[a][k].x);
+                    acc[a][k].y = fma(sv[a], y[k].y, acc[a][k].y);
+                }
+            if (ti == 0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    accb[k] = accb[k] + y[k];
+                    if (!CONJ) acct[k] += abs2(y[k]);
+                }
+            }
+            if (a_cta && t < TI) acca = acca + sg[q][t] * gs[q];
+            if (t == 0) {
+                accg = accg + gs[q];
+                accgg += abs2(gs[q]);
+            }
+        }
+    }
+    cpx<double>* out = (cpx<double>*)partial + (size_t)c * (P + 2 + M);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int j = j0 + tj + k;
+        if (j >= M) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = i0 + ti + a;
+            if (i < N) out[N + M + (size_t)i * M + j] = ccast<double>(acc[a][k]);
+        }
+        if (b_cta && ti == 0) {
+            out[N + j] = ccast<double>(accb[k]);
+            if (!CONJ) out[P + 2 + j] = {(double)acct[k], 0.0};
+        }
+    }
+    if (a_cta && t < TI && i0 + t < N) out[i0 + t] = ccast<double>(acca);
+    if (a_cta && b_cta && t == 0) {
+        out[P] = ccast<double>(accg);
+        out[P + 1] = {(double)accgg, 0.0};
+    }
+}
+
 // red[k] = sum over chunks of partial[c][k] (k < len, rows `stride` long), in chunk order.
 __global__ void combine_kernel(const double* __restrict__ partial, int n_chunks, int len,
                                int stride, double* __restrict__ red,
@@ -128,20 +252,14 @@ static cr_status oreduce_t(cr_ctx* c, const int8_t* spins, const void* T, const 
     const int nch = c->n_chunks < B ? c->n_chunks : B;
     const int chunk = (B + nch - 1) / nch;
     const int jpt = (M + 127) / 128;
-    const bool dbl = sizeof(R) == 8;
-#define LAUNCH(JPT, IT)                                                                            \
-    CR_LAUNCH(c, CR_KERNEL_REDUCE, oreduce_kernel<R, JPT, IT, CONJ><<<dim3(nch, (N + IT - 1) / IT), 128, 0, c->stream>>>(        \
-        spins, (const cpx<R>*)T, (const cpx<R>*)g, B, N, M, P, chunk, c->partial, skip))
-    if (jpt == 1) {
-        if (dbl) LAUNCH(1, 8); else LAUNCH(1, 16);
-    } else if (jpt == 2) {
-        if (dbl) LAUNCH(2, 4); else LAUNCH(2, 8);
-    } else {
-        if (dbl) LAUNCH(4, 2); else LAUNCH(4, 4);
-    }
-#undef LAUNCH
-    cr_status s = cr_check_launch(c, "oreduce_kernel");
+    (void)jpt;
+    CR_LAUNCH(c, CR_KERNEL_REDUCE,
+              oreduce2_kernel<R, CONJ><<<dim3(nch, (M + 31) / 32, (N + 63) / 64), 128, 0,
+                                         c->stream>>>(spins, (const cpx<R>*)T, (const cpx<R>*)g,
+                                                      B, N, M, P, chunk, c->partial, skip));
+    cr_status s = cr_check_launch(c, "oreduce2_kernel");
     if (s != CR_OK) return s;
+    if (!red_out) return CR_OK;  // the caller combines the chunk rows itself
     const int len = CONJ ? P + 2 : P + 2 + M;
     CR_LAUNCH(c, CR_K_OTHER, combine_kernel<<<(len + 255) / 256, 256, 0, c->stream>>>(
                                  c->partial, nch, len, P + 2 + M, red_out, skip));
@@ -365,7 +483,7 @@ __global__ void __launch_bounds__(1024) cg_init_kernel(const double* __restrict_
     ff = block_sum(ff, red);
     rz = block_sum(rz, red);
     if (threadIdx.x == 0) {
-        scal[0] = rz;
+        scal[5] = rz;
         scal[1] = ff;
         scal[2] = ff == 0.0 ? 1.0 : 0.0;
         scal[3] = 0.0;
@@ -373,57 +491,122 @@ __global__ void __launch_bounds__(1024) cg_init_kernel(const double* __restrict_
     }
 }
 
-// One CG step after red = [sum conj(O) u | sum u | .] for u = O p.
-template <typename R>
-__global__ void __launch_bounds__(1024) cg_step_kernel(const double* __restrict__ red_,
+// Multi-CTA CG step, three launches per iteration.  scal[5 + (it & 1)]
+// holds r.z of iteration it, so the last kernel writes the next value into
+// the other slot while its CTAs still read the current one.  Per-CTA partial
+// dot products go to part[3][nblk] and are summed by every CTA in the same
+// fixed order (deterministic).
+constexpr int CG_TPB = 256;
+
+__device__ double sum_parts(const double* p, int n, double* red) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) v += p[b];
+    return block_sum(v, red);
+}
+
+// Ap = S p + shift p from the chunk rows of sum conj(O) (O p) (the combine
+// fused in), and the per-CTA share of p.Ap.  A CTA takes 32 parameters; its
+// 8 warps each sum every 8th chunk row, then warp 0 adds the 8 group sums in
+// order (a fixed summation order, so the result is deterministic).
+constexpr int CGA_K = 32;
+
+__global__ void __launch_bounds__(256) cg_apply_kernel(const double* __restrict__ partial,
+                                                       int nch, int stride,
                                                        const double* __restrict__ redO_, int P,
-                                                       int B, double shift, double tol,
+                                                       int B, double shift,
                                                        double* __restrict__ cg_,
-                                                       cpx<R>* __restrict__ p_lo,
-                                                       double* __restrict__ scal) {
+                                                       double* __restrict__ part,
+                                                       const double* __restrict__ scal) {
+    if (scal[2] != 0.0) return;
+    __shared__ cpx<double> grp[8][CGA_K];
+    __shared__ cpx<double> smu;
+    const cpx<double>* pt = (const cpx<double>*)partial;
+    const cpx<double>* sO = (const cpx<double>*)redO_;
+    cpx<double>* p = (cpx<double>*)cg_ + 2 * P;
+    cpx<double>* Ap = (cpx<double>*)cg_ + 3 * P;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k = blockIdx.x * CGA_K + lane;
+    cpx<double> w = {0.0, 0.0};
+    if (k < P)
+        for (int c = wid; c < nch; c += 8) w = w + pt[(size_t)c * stride + k];
+    grp[wid][lane] = w;
+    if (wid == 7) {
+        cpx<double> su = {0.0, 0.0};
+        for (int c = lane; c < nch; c += 32) su = su + pt[(size_t)c * stride + P];
+        su = warp_sum(su);
+        if (lane == 0) smu = su;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const double inv = 1.0 / B;
+        double pap = 0.0;
+        if (k < P) {
+            cpx<double> tot = grp[0][lane];
+#pragma unroll
+            for (int gi = 1; gi < 8; ++gi) tot = tot + grp[gi][lane];
+            cpx<double> a = inv * tot - conj(inv * sO[k]) * (inv * smu) + shift * p[k];
+            Ap[k] = a;
+            pap = cmulc(p[k], a).x;
+        }
+        pap = warp_sum(pap);
+        if (lane == 0) part[blockIdx.x] = pap;
+    }
+}
+
+// alpha = r.z / p.Ap; x += alpha p; r -= alpha Ap; shares of r.r and r.z.
+__global__ void __launch_bounds__(CG_TPB) cg_xr_kernel(int P, double* __restrict__ cg_,
+                                                       double* __restrict__ part, int napp,
+                                                       int nblk, const double* __restrict__ scal,
+                                                       int slot) {
     if (scal[2] != 0.0) return;
     __shared__ double red[32];
-    const cpx<double>* sOu = (const cpx<double>*)red_;
-    const cpx<double>* sO = (const cpx<double>*)redO_;
     cpx<double>* x = (cpx<double>*)cg_;
     cpx<double>* r = x + P;
-    cpx<double>* p = x + 2 * P;
-    cpx<double>* Ap = x + 3 * P;
+    const cpx<double>* p = x + 2 * P;
+    const cpx<double>* Ap = x + 3 * P;
     const cpx<double>* dg = x + 4 * P;
-    const double inv = 1.0 / B;
-    const cpx<double> mu = inv * sOu[P];
-    double pap = 0.0;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
-        cpx<double> a = inv * sOu[k] - conj(inv * sO[k]) * mu + shift * p[k];
-        Ap[k] = a;
-        pap += cmulc(p[k], a).x;
-    }
-    pap = block_sum(pap, red);
-    const double rz = scal[0];
-    const double alpha = rz / pap;
-    double rn = 0.0;
-    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    const double alpha = scal[5 + slot] / sum_parts(part, napp, red);
+    part += napp;  // this kernel's shares follow the p.Ap shares
+    const int k = blockIdx.x * CG_TPB + threadIdx.x;
+    double rn = 0.0, rz = 0.0;
+    if (k < P) {
         x[k] = x[k] + alpha * p[k];
         cpx<double> rk = r[k] - alpha * Ap[k];
         r[k] = rk;
-        rn += abs2(rk);
+        rn = abs2(rk);
+        rz = (1.0 / dg[k].x) * rn;
     }
     rn = block_sum(rn, red);
-    const bool done = !(rn > tol * tol * scal[1]);
-    double rzn = 0.0;
-    if (!done) {
-        for (int k = threadIdx.x; k < P; k += blockDim.x) rzn += (1.0 / dg[k].x) * abs2(r[k]);
-        rzn = block_sum(rzn, red);
-        const double beta = rzn / rz;
-        for (int k = threadIdx.x; k < P; k += blockDim.x) {
-            cpx<double> pk = (1.0 / dg[k].x) * r[k] + beta * p[k];
-            p[k] = pk;
-            p_lo[k] = ccast<R>(pk);
-        }
-    }
-    __syncthreads();
+    rz = block_sum(rz, red);
     if (threadIdx.x == 0) {
-        scal[0] = rzn;
+        part[blockIdx.x] = rn;
+        part[nblk + blockIdx.x] = rz;
+    }
+}
+
+// Convergence test |r| <= tol |F|, then beta = r.z(new) / r.z and p = z + beta p.
+template <typename R>
+__global__ void __launch_bounds__(CG_TPB) cg_p_kernel(int P, double tol, double* __restrict__ cg_,
+                                                      cpx<R>* __restrict__ p_lo,
+                                                      double* __restrict__ part, int nblk,
+                                                      double* __restrict__ scal, int slot) {
+    if (scal[2] != 0.0) return;
+    __shared__ double red[32];
+    const cpx<double>* r = (const cpx<double>*)cg_ + P;
+    cpx<double>* p = (cpx<double>*)cg_ + 2 * P;
+    const cpx<double>* dg = (const cpx<double>*)cg_ + 4 * P;
+    const double rn = sum_parts(part, nblk, red);
+    const double rzn = sum_parts(part + nblk, nblk, red);
+    const bool done = !(rn > tol * tol * scal[1]);
+    const int k = blockIdx.x * CG_TPB + threadIdx.x;
+    if (!done && k < P) {
+        const double beta = rzn / scal[5 + slot];
+        cpx<double> pk = (1.0 / dg[k].x) * r[k] + beta * p[k];
+        p[k] = pk;
+        p_lo[k] = ccast<R>(pk);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scal[5 + (slot ^ 1)] = rzn;
         scal[3] += 1.0;
         scal[4] = rn;
         if (done) scal[2] = 1.0;
@@ -464,7 +647,6 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
     const int P = c->P;
     double* redR = c->red;
     double* redO = c->red + 2 * (P + 2 + c->M);
-    double* redU = c->red + 4 * (P + 2 + c->M);
     cr_status s = oreduce(c, true, spins, T, Rv, B, redR, nullptr);
     if (s != CR_OK) return s;
     s = oreduce(c, false, spins, T, nullptr, B, redO, nullptr);
@@ -489,14 +671,23 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
                                      c->cg, (cpx<R>*)c->p_lo, c->scal));
         if ((s = cr_check_launch(c, "cg_init")) != CR_OK) return s;
         const double* done = c->scal + 2;
+        const int nblk = (P + CG_TPB - 1) / CG_TPB;
+        const int napp = (P + CGA_K - 1) / CGA_K;
+        const int nch = c->n_chunks < B ? c->n_chunks : B;
         for (int it = 0; it < o->cg_maxit; ++it) {
             s = launch_ov(c, c->p_lo, spins, B, T, c->u_tmp, done);
             if (s != CR_OK) return s;
-            s = oreduce(c, true, spins, T, c->u_tmp, B, redU, done);
+            s = oreduce(c, true, spins, T, c->u_tmp, B, nullptr, done);
             if (s != CR_OK) return s;
-            CR_LAUNCH(c, CR_KERNEL_CG, cg_step_kernel<R><<<1, 1024, 0, c->stream>>>(redU, redO, P, B, o->shift, o->cg_tol,
-                                                         c->cg, (cpx<R>*)c->p_lo, c->scal));
-            if ((s = cr_check_launch(c, "cg_step")) != CR_OK) return s;
+            CR_LAUNCH(c, CR_KERNEL_CG, cg_apply_kernel<<<napp, 256, 0, c->stream>>>(
+                                           c->partial, nch, P + 2 + c->M, redO, P, B, o->shift,
+                                           c->cg, c->cgpart, c->scal));
+            CR_LAUNCH(c, CR_KERNEL_CG, cg_xr_kernel<<<nblk, CG_TPB, 0, c->stream>>>(
+                                           P, c->cg, c->cgpart, napp, nblk, c->scal, it & 1));
+            CR_LAUNCH(c, CR_KERNEL_CG, cg_p_kernel<R><<<nblk, CG_TPB, 0, c->stream>>>(
+                                           P, o->cg_tol, c->cg, (cpx<R>*)c->p_lo,
+                                           c->cgpart + napp, nblk, c->scal, it & 1));
+            if ((s = cr_check_launch(c, "cg step")) != CR_OK) return s;
         }
     }
     CR_LAUNCH(c, CR_K_OTHER, apply_update_kernel<R><<<(P + 255) / 256, 256, 0, c->stream>>>(
