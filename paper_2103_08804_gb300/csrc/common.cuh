@@ -167,6 +167,7 @@ struct cr_ctx {
     cr_prec prec;
     int max_walkers, flags;
     int n_chunks;            // walker chunks of the reductions
+    int n_sm;                // multiprocessors of the device
     cudaStream_t stream;
     char err[512];
 

@@ -158,6 +158,10 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
         cr_destroy(c);
         return e == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;
     }
+    int dev = 0;
+    c->n_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
     std::vector<int2> bonds = make_bonds(c->Lx, c->Ly);
     e = cudaMemcpy(c->d_bonds, bonds.data(), Nb * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));

@@ -12,6 +12,11 @@
 
 cr_status launch_ov(cr_ctx* c, const void* v, const int8_t* spins, int B, const void* T, void* u,
                     const double* skip);
+bool tc_supported(const cr_ctx* c);
+cr_status launch_ov_tc(cr_ctx* c, const void* v, const int8_t* spins, int B, const void* T,
+                       void* u, const double* skip);
+cr_status launch_oreduce_tc(cr_ctx* c, const int8_t* spins, const void* T, const void* g, int B,
+                            const double* skip, int* nch_out);
 cr_status logderiv_impl(cr_ctx* ctx, const int8_t* spins, const void* theta, int B, void* tanh_out,
                         void* O_out);
 
@@ -673,11 +678,18 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
         const double* done = c->scal + 2;
         const int nblk = (P + CG_TPB - 1) / CG_TPB;
         const int napp = (P + CGA_K - 1) / CGA_K;
-        const int nch = c->n_chunks < B ? c->n_chunks : B;
+        const bool tcp = tc_supported(c);  // mixed precision: tensor-core products
+        int nch = c->n_chunks < B ? c->n_chunks : B;
         for (int it = 0; it < o->cg_maxit; ++it) {
-            s = launch_ov(c, c->p_lo, spins, B, T, c->u_tmp, done);
-            if (s != CR_OK) return s;
-            s = oreduce(c, true, spins, T, c->u_tmp, B, nullptr, done);
+            if (tcp) {
+                s = launch_ov_tc(c, c->p_lo, spins, B, T, c->u_tmp, done);
+                if (s != CR_OK) return s;
+                s = launch_oreduce_tc(c, spins, T, c->u_tmp, B, done, &nch);
+            } else {
+                s = launch_ov(c, c->p_lo, spins, B, T, c->u_tmp, done);
+                if (s != CR_OK) return s;
+                s = oreduce(c, true, spins, T, c->u_tmp, B, nullptr, done);
+            }
             if (s != CR_OK) return s;
             CR_LAUNCH(c, CR_KERNEL_CG, cg_apply_kernel<<<napp, 256, 0, c->stream>>>(
                                            c->partial, nch, P + 2 + c->M, redO, P, B, o->shift,

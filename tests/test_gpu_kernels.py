@@ -18,7 +18,10 @@ from paper_2103_08804_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-PRECS = {"fp64": (0, torch.complex128, 1e-10, 1e-10), "fp32": (1, torch.complex64, 2e-4, 1e-4)}
+PRECS = {"fp64": (0, torch.complex128, 1e-10, 1e-10), "fp32": (1, torch.complex64, 2e-4, 1e-4),
+         # mixed: the CG products on the tensor cores (sigma exact in bf16, the
+         # other operand split into three bf16 terms): float32-like accuracy
+         "mixed": (2, torch.complex64, 2e-4, 1e-4)}
 # (Lx, Ly, alpha, sigma, walkers): several tiles of every kernel plus a ragged tail
 CASES = [(12, 1, 1, 0.05, 1024), (4, 3, 2, 0.1, 333), (8, 1, 3, 0.1, 37), (64, 1, 2, 0.02, 517)]
 
@@ -197,8 +200,9 @@ def test_sr_step_cholesky(prec):
     assert relerr(d_gpu, info["delta"]) < (1e-9 if prec == "fp64" else 2e-3)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("shape", [(12, 1, 12, 1024), (16, 1, 32, 2000)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("shape", [(12, 1, 12, 1024), (16, 1, 32, 2000), (64, 1, 128, 700),
+                                   (10, 1, 20, 333)])
 @pytest.mark.parametrize("jacobi", [False, True])
 def test_sr_step_cg_matches_oracle_cg(prec, shape, jacobi):
     """float64: the matrix-free (preconditioned) CG against the oracle's
@@ -210,7 +214,7 @@ def test_sr_step_cg_matches_oracle_cg(prec, shape, jacobi):
     N = Lx * Ly
     p, cd, _, _ = PRECS[prec]
     params, spins, O, R = _sr_inputs(Lx, Ly, M, B, 30)
-    shift = 1e-2
+    shift = 1e-2 if M <= 32 else 1.0
     tol = 1e-10 if prec == "fp64" else 1e-5
     _, info = sr.sr_step(params, O, R, shift, 0.5, solver="cg", cg_maxit=300, cg_tol=tol,
                          jacobi=jacobi)
@@ -224,12 +228,14 @@ def test_sr_step_cg_matches_oracle_cg(prec, shape, jacobi):
     ctx.sync_status()
     st = host(stats)
     d_gpu = host(pr).astype(np.complex128) - params
+    ev = np.linalg.eigvalsh(info["S"]) + shift
     if prec == "fp64":
-        # after a long plateau near the threshold the two may stop a few steps apart
+        # after a long plateau near the threshold the two may stop a few steps apart;
+        # two solves that stop at |r| <= tol |F| each lie within kappa tol of the
+        # solution, so they may differ by 2 kappa tol
         assert abs(st[5] - its) <= max(1, 0.05 * its)
-        assert relerr(d_gpu, info["delta"]) < 1e-8
+        assert relerr(d_gpu, info["delta"]) < max(1e-8, 2 * (ev[-1] / ev[0]) * tol)
     else:
-        ev = np.linalg.eigvalsh(info["S"]) + shift
         x_exact = sr.shifted_solve(info["S"], info["F"], shift)
         assert st[6] <= tol
         assert relerr(d_gpu, x_exact) < (ev[-1] / ev[0]) * 1e-5

@@ -213,11 +213,12 @@ SOLVERS = {"cholesky": dict(solver="cholesky"),
                                       ("fp64-cg", (1e-5, 1e-3, 1e-3)),
                                       ("fp64-pcg", (1e-4, 1e-2, 1e-2)),
                                       ("fp32-cholesky", (2e-4, 0.1, 2e-2)),
-                                      ("fp32-pcg", (4e-3, 0.5, 0.2))])
+                                      ("fp32-pcg", (4e-3, 0.5, 0.2)),
+                                      ("mixed-pcg", (4e-3, 0.5, 0.2))])
 def test_single_projection_step_replay(e0, recorded, path, tol):
     from paper_2103_08804_gb300 import api
     prec_s, sol = path.split("-")
-    prec = api.FP64 if prec_s == "fp64" else api.FP32
+    prec = {"fp64": api.FP64, "fp32": api.FP32, "mixed": api.MIXED}[prec_s]
     solver = api.SOLVE_CHOLESKY if sol == "cholesky" else api.SOLVE_CG
     cg_tol = 1e-10 if prec == api.FP64 else 1e-5
     seq, _ = _seq(prec, e0, WL.moments, solver, cg_tol=cg_tol, cg_maxit=400,
