@@ -43,25 +43,33 @@ CR_D uint4 pack8(const __nv_bfloat16* v) {
 
 // ------------------------------------------------------------------ O v
 //
-// Shared memory: Bs [NT][3][NCp x Kp] (V_W split, column n = 2 j + re/im,
-// K = sites), As [128 x Kp] (the spins of one 128-walker tile), vb [M],
-// va [N], one mbarrier and the TMEM address slot.  A CTA loops over walker
-// tiles; D = sigma V for a tile occupies TMEM columns [256 nt, 256 nt + NCp).
-__global__ void __launch_bounds__(128, 1) ov_tc_kernel(
+// 256 threads.  Shared memory: Bs [NT][3][NCp x Kp] (V_W split, column
+// n = 2 j + re/im, K = sites), As [128 x Kp] (spins of one 128-walker tile),
+// Ts [2][128 x (TJC + 1)] (T of the tile, TJC complex columns at a time,
+// double-buffered, padded rows), vb [M], va [N], part [2][128], one mbarrier
+// and the TMEM slot.  A CTA loops over walker tiles; D = sigma V of a tile
+// occupies TMEM columns [256 nt, 256 nt + NCp).  Warps w and w + 4 read the
+// same TMEM lanes (rows), each half of every TJC-column chunk.
+constexpr int OV_THREADS = 256;
+constexpr int TJC = 32;  // complex columns of T per staged chunk
+
+__global__ void __launch_bounds__(OV_THREADS, 1) ov_tc_kernel(
     const cpx<float>* __restrict__ v, const int8_t* __restrict__ spins,
     const cpx<float>* __restrict__ T, int B, int N, int M, int Kp, int NCp, int NT,
     int tmem_cols, cpx<float>* __restrict__ u, const double* __restrict__ skip,
     int* __restrict__ status) {
     if (skip && *skip != 0.0) return;
     extern __shared__ __align__(1024) unsigned char sm[];
-    const size_t bsz = (size_t)NCp * Kp * 2;          // one split of one n-tile
+    const size_t bsz = (size_t)NCp * Kp * 2;
     unsigned char* Bs = sm;
     unsigned char* As = sm + (size_t)NT * 3 * bsz;
-    cpx<float>* vb = (cpx<float>*)(As + (size_t)128 * Kp * 2);
+    cpx<float>* Ts = (cpx<float>*)(As + (size_t)128 * Kp * 2);       // [2][128][TJC + 1]
+    cpx<float>* vb = Ts + 2 * 128 * (TJC + 1);
     cpx<float>* va = vb + M;
-    uint64_t* mbar = (uint64_t*)(((uintptr_t)(va + N) + 15) & ~(uintptr_t)15);
+    cpx<float>* part = va + N;                                         // [2][128]
+    uint64_t* mbar = (uint64_t*)(((uintptr_t)(part + 256) + 15) & ~(uintptr_t)15);
     uint32_t* slot = (uint32_t*)(mbar + 1);
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (t == 0) {
         tc::mbar_init(mbar, 1);
         tc::fence_mbar_init();
@@ -70,9 +78,8 @@ __global__ void __launch_bounds__(128, 1) ov_tc_kernel(
         tc::tmem_alloc(slot, (uint32_t)tmem_cols);
         tc::tmem_relinquish();
     }
-    // V_W in three bf16 terms, K-major (sites contiguous per column)
     const int kc_n = Kp / 8;
-    for (int e = t; e < NT * NCp * kc_n; e += 128) {
+    for (int e = t; e < NT * NCp * kc_n; e += OV_THREADS) {
         const int nt = e / (NCp * kc_n), rem = e % (NCp * kc_n), c = rem / kc_n, kc = rem % kc_n;
         const int j = nt * 128 + (c >> 1);
         __nv_bfloat16 h[8], m[8], l[8];
@@ -92,33 +99,61 @@ __global__ void __launch_bounds__(128, 1) ov_tc_kernel(
         *reinterpret_cast<uint4*>(base + bsz + off) = pack8(m);
         *reinterpret_cast<uint4*>(base + 2 * bsz + off) = pack8(l);
     }
-    for (int j = t; j < M; j += 128) vb[j] = v[N + j];
-    for (int i = t; i < N; i += 128) va[i] = v[i];
+    for (int j = t; j < M; j += OV_THREADS) vb[j] = v[N + j];
+    for (int i = t; i < N; i += OV_THREADS) va[i] = v[i];
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *slot;
     const uint32_t idesc = tc::make_idesc_bf16(128, NCp);
     const int ntiles = (B + 127) / 128;
+    const int nchunk = (M + TJC - 1) / TJC;
+    const bool vec16 = (N % 16) == 0;
+    const int lb = warp & 3, half = warp >> 2;   // TMEM lane block, column half
+    const int row = 32 * lb + lane;
     bool ok = true;
     int it = 0;
+    // T chunk ch of tile w0 into buffer b: consecutive threads take consecutive columns
+    auto load_T = [&](int w0, int ch, int b) {
+        cpx<float>* dst = Ts + (size_t)b * 128 * (TJC + 1);
+        for (int e = t; e < 128 * TJC; e += OV_THREADS) {
+            const int r = e / TJC, jj = e % TJC, w = w0 + r, j = ch * TJC + jj;
+            dst[r * (TJC + 1) + jj] = (w < B && j < M) ? T[(size_t)w * M + j] : cpx<float>{0.f, 0.f};
+        }
+    };
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-        const int w = tile * 128 + t;
-        cpx<float> ua = {0.f, 0.f};
-        for (int kc = 0; kc < kc_n; ++kc) {
-            __nv_bfloat16 s8[8];
+        const int w0 = tile * 128;
+        // spins of the tile: two threads per walker, each half of the sites
+        {
+            const int r = t >> 1, hh = t & 1, w = w0 + r;
+            cpx<float> ua = {0.f, 0.f};
+            for (int kc = hh * (kc_n / 2); kc < (hh + 1) * (kc_n / 2) + (hh ? kc_n % 2 : 0); ++kc) {
+                int8_t sv[8];
+                if (vec16 && w < B && kc * 8 + 8 <= N) {
+                    uint2 raw = *reinterpret_cast<const uint2*>(spins + (size_t)w * N + kc * 8);
+                    memcpy(sv, &raw, 8);
+                } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = kc * 8 + q;
-                const int sv = (w < B && k < N) ? spins[(size_t)w * N + k] : 0;
-                s8[q] = __float2bfloat16_rn((float)sv);
-                if (sv) ua = ua + (float)sv * va[k];
+                    for (int q = 0; q < 8; ++q) {
+                        const int k = kc * 8 + q;
+                        sv[q] = (w < B && k < N) ? spins[(size_t)w * N + k] : (int8_t)0;
+                    }
+                }
+                __nv_bfloat16 s8[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    s8[q] = __float2bfloat16_rn((float)sv[q]);
+                    if (sv[q]) ua = ua + (float)sv[q] * va[kc * 8 + q];
+                }
+                *reinterpret_cast<uint4*>(As + tc::kmajor_offset(r, kc * 8, Kp)) = pack8(s8);
             }
-            *reinterpret_cast<uint4*>(As + tc::kmajor_offset(t, kc * 8, Kp)) = pack8(s8);
+            ua.x += __shfl_xor_sync(0xffffffffu, ua.x, 1);
+            ua.y += __shfl_xor_sync(0xffffffffu, ua.y, 1);
+            if (hh == 0) part[r] = ua;
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
-        __syncthreads();  // As written; the previous tile's TMEM reads are done
+        __syncthreads();  // As written; the previous tile's TMEM and Ts reads are done
         tc::fence_after_sync();
         if (t == 0) {
             for (int nt = 0; nt < NT; ++nt)
@@ -131,23 +166,35 @@ __global__ void __launch_bounds__(128, 1) ov_tc_kernel(
                     }
             tc::commit(mbar);
         }
+        load_T(w0, 0, 0);  // overlaps the MMA
         ok = tc::mbar_wait(mbar, it & 1, WAIT_LIMIT) && ok;
         tc::fence_after_sync();
-        cpx<float> acc = ua;
-        for (int nt = 0; nt < NT; ++nt)
-            for (int ch = 0; ch < NCp / 16; ++ch) {
+        cpx<float> acc = {0.f, 0.f};
+        for (int ch = 0; ch < nchunk; ++ch) {
+            __syncthreads();  // chunk ch staged; buffer (ch + 1) & 1 free
+            if (ch + 1 < nchunk) load_T(w0, ch + 1, (ch + 1) & 1);
+            const cpx<float>* tr = Ts + (size_t)(ch & 1) * 128 * (TJC + 1) + row * (TJC + 1);
+            // this warp's half of the chunk: TJC / 2 complex = TJC fp32 columns
+            const int j_first = ch * TJC + half * (TJC / 2);
+            const int col0 = (j_first / 128) * 256 + 2 * (j_first % 128);
+#pragma unroll
+            for (int g = 0; g < TJC / 16; ++g) {
                 float d[16];
-                tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + nt * 256 + ch * 16, d);
+                tc::tmem_ld16(taddr + ((uint32_t)(32 * lb) << 16) + col0 + 16 * g, d);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int j = nt * 128 + ch * 8 + q;
-                    if (j < M && w < B) {
+                    const int jj = half * (TJC / 2) + 8 * g + q, j = ch * TJC + jj;
+                    if (j < M) {
                         cpx<float> x = {d[2 * q] + vb[j].x, d[2 * q + 1] + vb[j].y};
-                        acc = acc + T[(size_t)w * M + j] * x;
+                        acc = acc + tr[jj] * x;
                     }
                 }
             }
-        if (w < B) u[w] = acc;
+        }
+        if (half == 1) part[128 + row] = acc;
+        __syncthreads();
+        if (half == 0 && w0 + row < B) u[w0 + row] = part[row] + acc + part[128 + row];
+        __syncthreads();  // part[] and Ts are rewritten by the next tile
     }
     if (!ok && t == 0) set_status(status, CR_ETIMEOUT);
     tc::fence_before_sync();
@@ -157,28 +204,34 @@ __global__ void __launch_bounds__(128, 1) ov_tc_kernel(
 
 // ------------------------------------------------------- O^dag g reduction
 //
-// One CTA per (walker chunk, tile of 128 sites).  Per stage of 32 walkers:
-// As [128 x 32] = sigma^T (sites x walkers), Bs [NT][3][NCp x 32] = the bf16
-// terms of Y^T, Y_sj = conj(T_sj) g_s.  D accumulates over the chunk in TMEM.
-__global__ void __launch_bounds__(128, 1) oreduce_tc_kernel(
+// 256 threads; one CTA per (walker chunk, tile of 128 sites).  Per stage of
+// KC = 32 walkers, buffer b = stage & 1: As[b] [128 x 32] = sigma^T (sites x
+// walkers), Bs[b] [NT][3][NCp x 32] = the bf16 terms of Y^T, Y_sj =
+// conj(T_sj) g_s.  D accumulates over the chunk in TMEM; the MMAs of stage s
+// run while stage s + 1 is staged into the other buffer.
+constexpr int RED_THREADS = 256;
+
+__global__ void __launch_bounds__(RED_THREADS, 1) oreduce_tc_kernel(
     const int8_t* __restrict__ spins, const cpx<float>* __restrict__ T,
     const cpx<float>* __restrict__ g, int B, int N, int M, int P, int chunk, int NCp, int NT,
     int tmem_cols, double* __restrict__ partial, const double* __restrict__ skip,
     int* __restrict__ status) {
     if (skip && *skip != 0.0) return;
-    constexpr int KC = 32;
+    constexpr int KC = 32, HK = 16;  // walkers per stage, per thread half
     extern __shared__ __align__(1024) unsigned char sm[];
     const size_t bsz = (size_t)NCp * KC * 2;
-    unsigned char* Bs = sm;
-    unsigned char* As = sm + (size_t)NT * 3 * bsz;
-    cpx<float>* gs = (cpx<float>*)(As + 128 * KC * 2);
-    uint64_t* mbar = (uint64_t*)(gs + KC);
-    uint32_t* slot = (uint32_t*)(mbar + 1);
-    const int t = threadIdx.x, warp = t >> 5;
+    const size_t stage_bytes = (size_t)NT * 3 * bsz + 128 * KC * 2;
+    cpx<float>* gs = (cpx<float>*)(sm + 2 * stage_bytes);               // [2][KC]
+    cpx<float>* red = gs + 2 * KC;                                       // [2][128] x 2
+    uint64_t* mbar = (uint64_t*)(red + 4 * 128);                        // [2]
+    uint32_t* slot = (uint32_t*)(mbar + 2);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int c = blockIdx.x, i0 = blockIdx.y * 128;
     const int s0 = c * chunk, s1 = min(B, s0 + chunk);
+    const int r = t & 127, hh = t >> 7;   // site row / column, walker half
     if (t == 0) {
-        tc::mbar_init(mbar, 1);
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -194,44 +247,70 @@ __global__ void __launch_bounds__(128, 1) oreduce_tc_kernel(
     float accgg = 0.f;
     cpx<float> accb[2] = {{0.f, 0.f}, {0.f, 0.f}};
     bool ok = true;
-    int stage = 0;
-    for (int sb = s0; sb < s1; sb += KC, ++stage) {
+    const int i = i0 + r;
+    const int nstage = (s1 - s0 + KC - 1) / KC;
+    // register prefetch of one stage: HK spins of site i, HK x NT values of T
+    int8_t sp[HK];
+    cpx<float> tp[2][HK];
+    auto fetch = [&](int sb) {
+#pragma unroll
+        for (int q = 0; q < HK; ++q) {
+            const int s = sb + hh * HK + q;
+            sp[q] = (s < s1 && i < N) ? spins[(size_t)s * N + i] : (int8_t)0;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int j = nt * 128 + r;
+                tp[nt][q] = (nt < NT && s < s1 && j < M) ? T[(size_t)s * M + j]
+                                                         : cpx<float>{0.f, 0.f};
+            }
+        }
+    };
+    fetch(s0);
+    for (int stage = 0; stage < nstage; ++stage) {
+        const int sb = s0 + stage * KC, b = stage & 1;
+        unsigned char* Bs = sm + b * stage_bytes;
+        unsigned char* As = Bs + (size_t)NT * 3 * bsz;
+        cpx<float>* gsb = gs + b * KC;
+        // buffer b was read by the MMAs of stage - 2
+        if (stage >= 2) {
+            ok = tc::mbar_wait(&mbar[b], ((stage - 2) >> 1) & 1, WAIT_LIMIT) && ok;
+            tc::fence_after_sync();
+        }
         if (t < KC) {
             const int s = sb + t;
-            gs[t] = s < s1 ? g[s] : cpx<float>{0.f, 0.f};
+            gsb[t] = s < s1 ? g[s] : cpx<float>{0.f, 0.f};
         }
         __syncthreads();
-        // sigma^T: row t = site i0 + t, 32 walkers
-        const int i = i0 + t;
-        for (int kc = 0; kc < KC / 8; ++kc) {
+        // sigma^T row r (site i), walkers [hh HK, hh HK + HK)
+#pragma unroll
+        for (int kc = 0; kc < HK / 8; ++kc) {
             __nv_bfloat16 s8[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int s = sb + kc * 8 + q;
-                const int sv = (s < s1 && i < N) ? spins[(size_t)s * N + i] : 0;
-                s8[q] = __float2bfloat16_rn((float)sv);
-                if (sv) acca = acca + (float)sv * gs[kc * 8 + q];
+                const int qq = kc * 8 + q;
+                s8[q] = __float2bfloat16_rn((float)sp[qq]);
+                if (sp[qq]) acca = acca + (float)sp[qq] * gsb[hh * HK + qq];
             }
-            *reinterpret_cast<uint4*>(As + tc::kmajor_offset(t, kc * 8, KC)) = pack8(s8);
+            *reinterpret_cast<uint4*>(As + tc::kmajor_offset(r, hh * HK + kc * 8, KC)) = pack8(s8);
         }
-        // Y^T: complex column j = 128 nt + t (real columns 2t, 2t + 1 of n-tile nt)
-        for (int nt = 0; nt < NT; ++nt) {
-            const int j = nt * 128 + t;
-            if (2 * t >= NCp) break;  // columns past NCp do not exist in this tile
-            for (int kc = 0; kc < KC / 8; ++kc) {
+        // Y^T column j = 128 nt + r (real columns 2r, 2r + 1 of n-tile nt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            if (nt >= NT || 2 * r >= NCp) break;  // columns past NCp do not exist in this tile
+            unsigned char* base = Bs + (size_t)nt * 3 * bsz;
+#pragma unroll
+            for (int kc = 0; kc < HK / 8; ++kc) {
                 __nv_bfloat16 hr[8], mr[8], lr[8], hi_[8], mi[8], li[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int s = sb + kc * 8 + q;
-                    cpx<float> y = {0.f, 0.f};
-                    if (s < s1 && j < M) y = conj(T[(size_t)s * M + j]) * gs[kc * 8 + q];
+                    const int qq = kc * 8 + q;
+                    const cpx<float> y = conj(tp[nt][qq]) * gsb[hh * HK + qq];
                     accb[nt] = accb[nt] + y;
                     split3(y.x, &hr[q], &mr[q], &lr[q]);
                     split3(y.y, &hi_[q], &mi[q], &li[q]);
                 }
-                unsigned char* base = Bs + (size_t)nt * 3 * bsz;
-                const uint32_t o_re = tc::kmajor_offset(2 * t, kc * 8, KC);
-                const uint32_t o_im = tc::kmajor_offset(2 * t + 1, kc * 8, KC);
+                const uint32_t o_re = tc::kmajor_offset(2 * r, hh * HK + kc * 8, KC);
+                const uint32_t o_im = tc::kmajor_offset(2 * r + 1, hh * HK + kc * 8, KC);
                 *reinterpret_cast<uint4*>(base + o_re) = pack8(hr);
                 *reinterpret_cast<uint4*>(base + bsz + o_re) = pack8(mr);
                 *reinterpret_cast<uint4*>(base + 2 * bsz + o_re) = pack8(lr);
@@ -242,53 +321,69 @@ __global__ void __launch_bounds__(128, 1) oreduce_tc_kernel(
         }
         if (t == 0)
             for (int q = 0; q < KC; ++q) {
-                accg = accg + gs[q];
-                accgg += abs2(gs[q]);
+                accg = accg + gsb[q];
+                accgg += abs2(gsb[q]);
             }
+        if (stage + 1 < nstage) fetch(sb + KC);  // in flight during the MMAs
         tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
         if (t == 0) {
             for (int nt = 0; nt < NT; ++nt)
-                for (int sp = 0; sp < 3; ++sp)
+                for (int spl = 0; spl < 3; ++spl)
                     for (int ks = 0; ks < KC / 16; ++ks) {
                         const uint64_t ad = tc::make_desc(tc::smem_u32(As) + ks * 256, 128, 16 * KC);
                         const uint64_t bd = tc::make_desc(
-                            tc::smem_u32(Bs + ((size_t)nt * 3 + sp) * bsz) + ks * 256, 128, 16 * KC);
-                        tc::mma_bf16(taddr + nt * 256, ad, bd, idesc, (stage | sp | ks) != 0);
+                            tc::smem_u32(Bs + ((size_t)nt * 3 + spl) * bsz) + ks * 256, 128, 16 * KC);
+                        tc::mma_bf16(taddr + nt * 256, ad, bd, idesc, (stage | spl | ks) != 0);
                     }
-            tc::commit(mbar);
+            tc::commit(&mbar[b]);
         }
-        // the operands are rewritten next stage: wait for these MMAs
-        ok = tc::mbar_wait(mbar, stage & 1, WAIT_LIMIT) && ok;
+    }
+    // the last commit covers every earlier MMA of this thread
+    if (nstage > 0) {
+        const int last = nstage - 1;
+        ok = tc::mbar_wait(&mbar[last & 1], (last >> 1) & 1, WAIT_LIMIT) && ok;
         tc::fence_after_sync();
     }
+    // combine the two walker halves of the a- and b-sums
+    red[hh * 128 + r] = acca;
+    red[256 + hh * 128 + r] = accb[0];
+    __syncthreads();
     cpx<double>* out = (cpx<double>*)partial + (size_t)c * (P + 2 + M);
-    // D row t = site i0 + t
-    const int i = i0 + t;
+    if (hh == 0) {
+        if (i < N) out[i] = ccast<double>(red[r] + red[128 + r]);
+        if (blockIdx.y == 0) {
+            const int j = r;
+            if (j < M) out[N + j] = ccast<double>(red[256 + r] + red[384 + r]);
+        }
+    }
+    __syncthreads();
+    if (NT > 1) {
+        red[hh * 128 + r] = accb[1];
+        __syncthreads();
+        if (hh == 0 && blockIdx.y == 0 && 128 + r < M)
+            out[N + 128 + r] = ccast<double>(red[r] + red[128 + r]);
+    }
+    if (blockIdx.y == 0 && t == 0) {
+        out[P] = ccast<double>(accg);
+        out[P + 1] = {(double)accgg, 0.0};
+    }
+    // D rows: warps w and w + 4 read the same TMEM lanes, each half of the columns
+    const int lb = warp & 3, half = warp >> 2, row = 32 * lb + lane, ir = i0 + row;
+    const int nch16 = NCp / 16;
     for (int nt = 0; nt < NT; ++nt)
-        for (int ch = 0; ch < NCp / 16; ++ch) {
+        for (int ch = half * (nch16 / 2); ch < (half + 1) * (nch16 / 2) + (half ? nch16 % 2 : 0); ++ch) {
             float d[16];
-            tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + nt * 256 + ch * 16, d);
+            tc::tmem_ld16(taddr + ((uint32_t)(32 * lb) << 16) + nt * 256 + ch * 16, d);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int j = nt * 128 + ch * 8 + q;
-                if (i < N && j < M)
-                    out[N + M + (size_t)i * M + j] = {(double)d[2 * q], (double)d[2 * q + 1]};
+                if (ir < N && j < M)
+                    out[N + M + (size_t)ir * M + j] = {(double)d[2 * q], (double)d[2 * q + 1]};
             }
         }
-    if (i < N) out[i] = ccast<double>(acca);
-    if (blockIdx.y == 0) {
-        for (int nt = 0; nt < NT; ++nt) {
-            const int j = nt * 128 + t;
-            if (j < M) out[N + j] = ccast<double>(accb[nt]);
-        }
-        if (t == 0) {
-            out[P] = ccast<double>(accg);
-            out[P + 1] = {(double)accgg, 0.0};
-        }
-    }
     if (!ok && t == 0) set_status(status, CR_ETIMEOUT);
     tc::fence_before_sync();
     __syncthreads();
@@ -308,13 +403,14 @@ size_t ov_tc_smem(const cr_ctx* c) {
     int NCp, NT;
     tc_geometry(c->M, &NCp, &NT);
     const int Kp = ((c->N + 15) / 16) * 16;
-    return (size_t)NT * 3 * NCp * Kp * 2 + (size_t)128 * Kp * 2 + (size_t)(c->M + c->N) * 8 + 64;
+    return (size_t)NT * 3 * NCp * Kp * 2 + (size_t)128 * Kp * 2 +
+           (size_t)2 * 128 * (TJC + 1) * 8 + (size_t)(c->M + c->N + 256) * 8 + 64;
 }
 
 size_t oreduce_tc_smem(const cr_ctx* c) {
     int NCp, NT;
     tc_geometry(c->M, &NCp, &NT);
-    return (size_t)NT * 3 * NCp * 32 * 2 + 128 * 32 * 2 + 32 * 8 + 64;
+    return 2 * ((size_t)NT * 3 * NCp * 32 * 2 + 128 * 32 * 2) + 2 * 32 * 8 + 4 * 128 * 8 + 64;
 }
 
 // Whether the tensor-core kernels cover this context (M <= 256 and the
@@ -334,7 +430,7 @@ cr_status launch_ov_tc(cr_ctx* c, const void* v, const int8_t* spins, int B, con
     const int ntiles = (B + 127) / 128;
     const int grid = ntiles < c->n_sm ? ntiles : c->n_sm;
     CR_LAUNCH(c, CR_KERNEL_OV,
-              ov_tc_kernel<<<grid, 128, sm, c->stream>>>(
+              ov_tc_kernel<<<grid, OV_THREADS, sm, c->stream>>>(
                   (const cpx<float>*)v, spins, (const cpx<float>*)T, B, c->N, c->M, Kp, NCp, NT,
                   cols, (cpx<float>*)u, skip, c->d_status));
     return cr_check_launch(c, "ov_tc_kernel");
@@ -352,7 +448,7 @@ cr_status launch_oreduce_tc(cr_ctx* c, const int8_t* spins, const void* T, const
     const size_t sm = oreduce_tc_smem(c);
     cudaFuncSetAttribute(oreduce_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     CR_LAUNCH(c, CR_KERNEL_REDUCE,
-              oreduce_tc_kernel<<<dim3(nch, (c->N + 127) / 128), 128, sm, c->stream>>>(
+              oreduce_tc_kernel<<<dim3(nch, (c->N + 127) / 128), RED_THREADS, sm, c->stream>>>(
                   spins, (const cpx<float>*)T, (const cpx<float>*)g, B, c->N, c->M, c->P, chunk,
                   NCp, NT, cols, c->partial, skip, c->d_status));
     *nch_out = nch;
