@@ -37,7 +37,6 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "mixed"])
     ap.add_argument("--cg-maxit", type=int, default=50)
     ap.add_argument("--cg-tol", type=float, default=1e-4)
     ap.add_argument("--jacobi", action="store_true", help="Jacobi-preconditioned CG")
@@ -45,6 +44,10 @@ def parse():
                     help="natural-gradient iterations per moment (profiling runs only; the "
                          "workload's own count otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the replayed moment-error check against the float64 path")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch every kernel from the host instead of replaying CUDA graphs")
     ap.add_argument("--cpu-walkers", type=int, default=2048)
     return ap.parse_args()
 
@@ -152,43 +155,50 @@ def reduce_flops(wl):
     return B * (4 * N * M + 8 * M + 4 * N)
 
 
-def run_ours(args):
+def reduce_bytes(wl):
+    """Algorithmic bytes of one launch of the O-reduction: tanh(theta) (complex64
+    [B][M]), spins (int8 [B][N]) and g (complex64 [B]) in, the P-row of sums out
+    (complex128)."""
+    B, N, M = wl.walkers, wl.N, wl.M
+    P = N + M + N * M
+    return B * (8 * M + N + 8) + 16 * P
+
+
+def measure(args, prec_name, ws, rank, local):
+    """Time K moments of one precision path; returns (result dict, seq, ctx)."""
     import torch
 
     from paper_2103_08804_gb300 import api, driver, synth
 
-    ws, rank, local = dist_setup()
-    torch.cuda.set_device(local)
     wl = synth.WORKLOADS[WORKLOAD]
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
     K, W = args.steps, args.warmup
     n_moments = 1 + W + 2 * K
     seed = 1000 + 17 * rank
-    prec = api.FP32 if args.prec == "fp32" else api.MIXED
+    prec = {"fp32": api.FP32, "mixed": api.MIXED}[prec_name]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = api.Context(wl.Lx, wl.Ly, wl.M, wl.walkers, prec=prec, stream=stream)
     psi = synth.rbm_params(seed, wl.N, wl.M, wl.sigma)
     cfg = make_config(wl, E0, a, args, n_moments, seed)
     seq = driver.Sequence(ctx, cfg, psi, synth.sz0_spins(seed + 2, wl.walkers, wl.N),
-                          synth.sz0_spins(seed + 3, wl.walkers, wl.N))
+                          synth.sz0_spins(seed + 3, wl.walkers, wl.N), graphs=not args.eager)
     seq.start()
     for n in range(1, 1 + W):
         seq.fit(n)
     ctx.sync_status()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    kernel = "reduce"
-    per_step_launches = None
-    ctx.time_kernel(kernel, 4096)
+    ctx.time_kernel("reduce", 4096)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
     barrier(ws)
     torch.cuda.synchronize()
-    launches0 = ctx.n_launches()
+    launches0 = ctx.n_launches() + seq.graph_launches
     wall0 = time.perf_counter()
-    with ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_r{rank}.csv")
-                      if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                      else f"/tmp/clocks_r{rank}.csv", local) as clk:
+    clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_{prec_name}_r{rank}.csv")
+                if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                else f"/tmp/clocks_{prec_name}_r{rank}.csv")
+    with ClockSampler(clk_path, local) as clk:
         for k in range(K):
             flush.zero_()
             ev[k][0].record(stream)
@@ -197,63 +207,144 @@ def run_ours(args):
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     barrier(ws)
-    launches = ctx.n_launches() - launches0
-    per_step_launches = launches / K
+    launches = ctx.n_launches() + seq.graph_launches - launches0
     ktimes = ctx.kernel_times()
+    if not ktimes:
+        # graph replays do not re-record host-side events: time the same kernel
+        # on eagerly launched iterations of the same step right after
+        for _ in range(3):
+            seq._iteration(3)
+        torch.cuda.synchronize()
+        ktimes = ctx.kernel_times()
     ctx.time_kernel(None, 1)
     ctx.sync_status()
     step_ms = [e[0].elapsed_time(e[1]) for e in ev]
     ms = max_over_ranks(ws, float(np.mean(step_ms)))
-    # stats of the timed moments
     st = seq.stats[1 + W:1 + W + K].cpu().numpy()
-    cg_iters = float(st[..., 5].mean())
-    # ------------------------------------------------------------ end to end
-    e2e_ms, Bi, Bo = e2e(seq, ctx, 1 + W + K, K, stream)
-    e2e_ms = max_over_ranks(ws, e2e_ms)
-    peaks, peak_src = measured_peaks()
     clocks = clk.summary()
     f_sm = clocks.get("sm_mhz") or 2070.0
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_sm * 1e6 / 1e12
     k_ms = float(np.mean(ktimes)) if ktimes else None
-    achieved = reduce_flops(wl) / (k_ms * 1e-3) / 1e12 if k_ms else None
+    peaks, peak_src = measured_peaks()
+    if prec_name == "fp32":
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_sm * 1e6 / 1e12
+        achieved = reduce_flops(wl) / (k_ms * 1e-3) / 1e12 if k_ms else None
+        roof = {"kernel": "oreduce2_kernel (sum_s sigma_si conj(T_sj) g_s, FP32 FMA)",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "work_per_launch": reduce_flops(wl),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}
+    else:
+        peak = float(peaks["hbm_gbs"])
+        achieved = reduce_bytes(wl) / (k_ms * 1e-3) / 1e9 if k_ms else None
+        roof = {"kernel": "oreduce_tc_kernel (tcgen05 bf16x3, split-K over walkers)",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "work_per_launch": reduce_bytes(wl),
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+    roof.update({"frac": (achieved / peak) if achieved else None, "traffic": None,
+                 "launches_timed": len(ktimes), "avg_launch_ms": k_ms})
     sweeps_per_moment = cfg.n_therm + cfg.n_iter * cfg.sweeps_per_iter + cfg.sweeps_per_iter
-    value = ws * 3600.0 * 1000.0 / ms
+    res = {"value": ws * 3600.0 * 1000.0 / ms, "ms_per_step": ms,
+           "mc_samples_per_s": ws * wl.walkers * sweeps_per_moment / (ms * 1e-3),
+           "gpu_launches": int(round(launches)), "gpu_launches_per_step": launches / K,
+           "cg_iters_mean": float(st[..., 5].mean()), "wall_s_timed": wall, "clocks": clocks,
+           "roofline": roof}
+    e2e_ms, Bi, Bo = e2e(seq, ctx, 1 + W + K, K, stream)
+    e2e_ms = max_over_ranks(ws, e2e_ms)
+    res["e2e"] = {"value": ws * 3600.0 * 1000.0 / e2e_ms, "unit": "moments/hour",
+                  "h2d_bytes_per_step": Bi, "d2h_bytes_per_step": Bo}
+    del flush
+    return res, cfg, wl
+
+
+def moment_error(args, n_moments=3, iters=10):
+    """Moment error (max_n |mu_n - mu_n^ref| / mu_0) of the mixed and plain
+    float32 paths on the bench workload, against the float64 GPU path on the
+    same walker configurations (replay of the float64 run's samples), over
+    moments 0 .. n_moments - 1 with `iters` natural-gradient iterations each."""
+    import torch
+
+    from paper_2103_08804_gb300 import api, driver, synth
+
+    wl = synth.WORKLOADS[WORKLOAD]
+    E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
+    seed = 4242
+
+    class _A:
+        pass
+
+    a_ = _A()
+    a_.cg_maxit, a_.cg_tol, a_.jacobi, a_.iters = args.cg_maxit, args.cg_tol, args.jacobi, iters
+    cfg = make_config(wl, E0, a, a_, n_moments, seed)
+    psi = synth.rbm_params(seed, wl.N, wl.M, wl.sigma)
+    s_fit = synth.sz0_spins(seed + 2, wl.walkers, wl.N)
+    s_ref = synth.sz0_spins(seed + 3, wl.walkers, wl.N)
+    torch.cuda.set_stream(torch.cuda.default_stream())
+    ref = driver.Sequence(api.Context(wl.Lx, wl.Ly, wl.M, wl.walkers, prec=api.FP64), cfg, psi,
+                          s_fit, s_ref)
+    ref.start()
+    rec = {}
+    for n in range(1, n_moments):
+        rec[n] = []
+        ref.fit(n, record=rec[n])
+    ref.ctx.sync_status()
+    mu_ref = ref.mu.cpu().numpy()
+    out = {}
+    for name, prec in (("mixed", api.MIXED), ("plain_fp32", api.FP32)):
+        seq = driver.Sequence(api.Context(wl.Lx, wl.Ly, wl.M, wl.walkers, prec=prec), cfg, psi,
+                              s_fit, s_ref)
+        seq.start(replay_ref=ref.spins_ref)
+        for n in range(1, n_moments):
+            seq.fit(n, replay=rec[n])
+        seq.ctx.sync_status()
+        out[name] = float(np.max(np.abs(seq.mu.cpu().numpy() - mu_ref)) / abs(mu_ref[0]))
+    out["reference"] = (f"float64 GPU path on the same samples (replay), moments 0..{n_moments - 1}, "
+                        f"{iters} natural-gradient iterations each, CG {args.cg_maxit}")
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    mixed, cfg, wl = measure(args, "mixed", ws, rank, local)
+    plain, _, _ = measure(args, "fp32", ws, rank, local)
+    merr = moment_error(args) if (rank == 0 and not args.no_accuracy) else None
     out = {
         "metric": "Chebyshev moments/hour",
-        "value": value,
+        "value": mixed["value"],
         "unit": "moments/hour",
         "n_gpus": ws,
-        "steps": K,
-        "warmup": W,
-        "ms_per_step": ms,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": mixed["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 (products), f64 (sums, CG)" if prec == api.FP32 else "mixed",
+        "dtype": "mixed: bf16x3 tensor-core contractions with f32 accumulation, f32 elsewhere, "
+                 "f64 sums and CG",
         "data": "synthetic (random complex RBM, sigma=0.02; seeded S^z=0 walkers)",
         "config": {"workload": "chain64: periodic Heisenberg chain N=64, RBM alpha=2 (M=128, "
                                "P=8384), 16384 walkers, q=pi/2, 50 natural-gradient iterations "
                                "per moment, matrix-free CG shifted solve",
-                   "path": "plain fp32" if prec == api.FP32 else "mixed",
-                   "walkers": wl.walkers, "iters_per_moment": cfg.n_iter,
+                   "path": "mixed", "walkers": wl.walkers, "iters_per_moment": cfg.n_iter,
                    "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol, "jacobi": args.jacobi,
-                   "cg_iters_mean": cg_iters, "l2": "256 MiB buffer written between timed steps",
+                   "l2": "256 MiB buffer written between timed steps",
+                   "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
                    "parallelism": f"replicas x{ws}"},
-        "mc_samples_per_s": ws * wl.walkers * sweeps_per_moment / (ms * 1e-3),
+        "mc_samples_per_s": mixed["mc_samples_per_s"],
         "mc_samples_unit": "walker-sweeps/s (one sweep = N exchange proposals)",
-        "gpu_launches": int(round(per_step_launches * K)),
-        "gpu_launches_per_step": per_step_launches,
-        "wall_s_timed": wall,
-        "clocks": clocks,
-        "e2e": {"value": ws * 3600.0 * 1000.0 / e2e_ms, "unit": "moments/hour",
-                "h2d_bytes_per_step": Bi, "d2h_bytes_per_step": Bo},
-        "roofline": {"kernel": "oreduce_kernel (sum_s op(O_k) g_s)", "bound": "alu",
-                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
-                     "launches_timed": len(ktimes), "avg_launch_ms": k_ms,
-                     "flops_per_launch": reduce_flops(wl),
-                     "peak_source": "FP32 lanes x 2 x median SM clock under load"},
-        "peaks_file": peak_src,
+        "gpu_launches": mixed["gpu_launches"],
+        "gpu_launches_per_step": mixed["gpu_launches_per_step"],
+        "cg_iters_mean": mixed["cg_iters_mean"],
+        "wall_s_timed": mixed["wall_s_timed"],
+        "clocks": mixed["clocks"],
+        "e2e": mixed["e2e"],
+        "roofline": mixed["roofline"],
+        "plain_fp32": {k: plain[k] for k in ("value", "ms_per_step", "mc_samples_per_s",
+                                              "gpu_launches_per_step", "cg_iters_mean", "e2e",
+                                              "roofline", "clocks")},
+        "mixed_over_plain": mixed["value"] / plain["value"],
+        "moment_error": merr,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)

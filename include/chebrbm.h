@@ -112,10 +112,15 @@ typedef struct {
 
 /* Counter-based random stream (Philox4x32-10, Salmon et al. SC'11).
    key = seed; counter = (walker, step lo, step hi, 0). Host struct; calls
-   that draw from it advance `counter` on the host, synchronously. */
+   that draw from it advance `counter` on the host, synchronously.  When
+   device_counter is non-NULL the stream position lives on the device
+   instead (one uint64): kernels read it there and the library advances it
+   on the context stream, so the calls can be captured in a CUDA graph and
+   replayed; `counter` is then ignored. */
 typedef struct {
     uint64_t seed;
     uint64_t counter;
+    uint64_t* device_counter;
 } cr_philox;
 
 /* The target of projection step n (Sec. III, last paragraph). */
@@ -191,8 +196,9 @@ cr_status rbm_logpsi(cr_ctx* ctx, const cr_state* state, const int8_t* spins, in
    (floor(u0 * N_b / 2^32)) and, if its spins are antiparallel, exchanges them
    with probability min(1, |psi(s')/psi(s)|^2), accepting iff
    ((u1 >> 9) + 1/2) / 2^23 < |psi(s')/psi(s)|^2. Proposal p of walker w uses
-   Philox call counter + p/2, words (2(p%2), 2(p%2)+1). rng->counter advances
-   by ceil(n_sweeps * N / 2). Total S^z is conserved.
+   Philox call counter + p/2, words (2(p%2), 2(p%2)+1). The stream position
+   (rng->counter, or *rng->device_counter) advances by ceil(n_sweeps * N / 2).
+   Total S^z is conserved.
    spins [B][N] in/out. theta [B][M] in/out: on entry it must equal
    b + sigma W for `state` (as written by rbm_logpsi); on exit it matches the
    new spins. logpsi_out [B] (NULL allowed), tanh_out [B][M] = tanh(theta)

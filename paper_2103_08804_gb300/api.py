@@ -40,7 +40,8 @@ class State(ctypes.Structure):
 
 
 class Philox(ctypes.Structure):
-    _fields_ = [("seed", ctypes.c_uint64), ("counter", ctypes.c_uint64)]
+    _fields_ = [("seed", ctypes.c_uint64), ("counter", ctypes.c_uint64),
+                ("device_counter", ctypes.c_void_p)]
 
 
 class Target(ctypes.Structure):

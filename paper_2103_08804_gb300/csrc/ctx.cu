@@ -6,6 +6,8 @@
 
 #include "common.cuh"
 
+cr_status tc_prepare(cr_ctx* c);
+
 cr_status cr_fail(cr_ctx* c, cr_status s, const char* fmt, ...) {
     if (c) {
         va_list ap;
@@ -166,7 +168,7 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
     e = cudaMemcpy(c->d_bonds, bonds.data(), Nb * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, 64 * sizeof(double));
-    if (e != cudaSuccess) {
+    if (e != cudaSuccess || tc_prepare(c) != CR_OK) {
         cr_destroy(c);
         return CR_ECUDA;
     }

@@ -15,8 +15,10 @@ __global__ void __launch_bounds__(128) sweep_kernel(
     const cpx<R>* __restrict__ prm, int8_t* __restrict__ spins, cpx<R>* __restrict__ theta, int B,
     int N, int M, int Mp, int Nb, const int2* __restrict__ bonds_g, const cpx<R>* __restrict__ Dt,
     const cpx<R>* __restrict__ Cht, const cpx<R>* __restrict__ Sht, const cpx<R>* __restrict__ ea,
-    int n_prop, uint32_t k0, uint32_t k1, unsigned long long counter, cpx<R>* __restrict__ logpsi_out,
+    int n_prop, uint32_t k0, uint32_t k1, unsigned long long counter,
+    const unsigned long long* __restrict__ dcounter, cpx<R>* __restrict__ logpsi_out,
     cpx<R>* __restrict__ tanh_out, int32_t* __restrict__ n_acc) {
+    if (dcounter) counter = *dcounter;  // stream position kept on the device
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int2* bonds = (int2*)smem_raw;                       // [Nb]
     int8_t* sg_all = (int8_t*)(bonds + Nb);              // [4][N]
@@ -108,10 +110,15 @@ __global__ void __launch_bounds__(128) sweep_kernel(
     }
 }
 
+// Advance a device-resident stream position (after the sweep that used it).
+__global__ void advance_counter_kernel(unsigned long long* ctr, unsigned long long calls) {
+    *ctr += calls;
+}
+
 template <typename R>
 static cr_status sweep_t(cr_ctx* c, const void* params, int8_t* spins, void* theta, int B,
-                         int n_prop, uint64_t seed, uint64_t counter, void* logpsi_out,
-                         void* tanh_out, int32_t* n_acc) {
+                         int n_prop, uint64_t seed, uint64_t counter, const uint64_t* dcounter,
+                         void* logpsi_out, void* tanh_out, int32_t* n_acc) {
     const cr_tables& t = c->tab[0];
     const int kpl = c->Mp / 32;
     size_t sm = c->Nb * sizeof(int2) + 4 * c->N;
@@ -120,8 +127,8 @@ static cr_status sweep_t(cr_ctx* c, const void* params, int8_t* spins, void* the
     CR_LAUNCH(c, CR_KERNEL_SWEEP, sweep_kernel<R, K><<<grid, 128, sm, c->stream>>>(                                             \
         (const cpx<R>*)params, spins, (cpx<R>*)theta, B, c->N, c->M, c->Mp, c->Nb, c->d_bonds,     \
         (const cpx<R>*)t.D, (const cpx<R>*)t.Ch, (const cpx<R>*)t.Sh, (const cpx<R>*)t.ea, n_prop, \
-        (uint32_t)seed, (uint32_t)(seed >> 32), (unsigned long long)counter, (cpx<R>*)logpsi_out,  \
-        (cpx<R>*)tanh_out, n_acc))
+        (uint32_t)seed, (uint32_t)(seed >> 32), (unsigned long long)counter,                        \
+        (const unsigned long long*)dcounter, (cpx<R>*)logpsi_out, (cpx<R>*)tanh_out, n_acc))
     switch (kpl) {
         case 1: LAUNCH(1); break;
         case 2: LAUNCH(2); break;
@@ -146,18 +153,24 @@ extern "C" cr_status mc_sweep(cr_ctx* ctx, const cr_state* st, int8_t* spins, vo
     CR_CHECK_ARG(ctx->Mp <= 512, "mc_sweep: M > 512 not supported");
     const int n_prop = n_sweeps * ctx->N;
     const uint64_t calls = (uint64_t)(n_prop + 1) / 2;
-    if (B == 0) {
-        rng->counter += calls;
-        return CR_OK;
+    if (B > 0) {
+        CR_CHECK_ARG(spins && theta, "mc_sweep: null spins or theta");
+        cr_status s = build_tables(ctx, st->params, 0);
+        if (s != CR_OK) return s;
+        s = ctx->prec == CR_FP64
+                ? sweep_t<double>(ctx, st->params, spins, theta, B, n_prop, rng->seed,
+                                  rng->counter, rng->device_counter, logpsi_out, tanh_out,
+                                  n_accepted)
+                : sweep_t<float>(ctx, st->params, spins, theta, B, n_prop, rng->seed,
+                                 rng->counter, rng->device_counter, logpsi_out, tanh_out,
+                                 n_accepted);
+        if (s != CR_OK) return s;
     }
-    CR_CHECK_ARG(spins && theta, "mc_sweep: null spins or theta");
-    cr_status s = build_tables(ctx, st->params, 0);
-    if (s != CR_OK) return s;
-    s = ctx->prec == CR_FP64
-            ? sweep_t<double>(ctx, st->params, spins, theta, B, n_prop, rng->seed, rng->counter,
-                              logpsi_out, tanh_out, n_accepted)
-            : sweep_t<float>(ctx, st->params, spins, theta, B, n_prop, rng->seed, rng->counter,
-                             logpsi_out, tanh_out, n_accepted);
-    if (s == CR_OK) rng->counter += calls;
-    return s;
+    if (rng->device_counter) {
+        CR_LAUNCH(ctx, CR_K_OTHER, advance_counter_kernel<<<1, 1, 0, ctx->stream>>>(
+                                       (unsigned long long*)rng->device_counter, calls));
+        return cr_check_launch(ctx, "advance_counter_kernel");
+    }
+    rng->counter += calls;
+    return CR_OK;
 }

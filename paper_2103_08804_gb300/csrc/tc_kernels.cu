@@ -426,7 +426,6 @@ cr_status launch_ov_tc(cr_ctx* c, const void* v, const int8_t* spins, int B, con
     const int cols = tc_geometry(c->M, &NCp, &NT);
     const int Kp = ((c->N + 15) / 16) * 16;
     const size_t sm = ov_tc_smem(c);
-    cudaFuncSetAttribute(ov_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int ntiles = (B + 127) / 128;
     const int grid = ntiles < c->n_sm ? ntiles : c->n_sm;
     CR_LAUNCH(c, CR_KERNEL_OV,
@@ -446,11 +445,22 @@ cr_status launch_oreduce_tc(cr_ctx* c, const int8_t* spins, const void* T, const
     const int chunk = (B + nch0 - 1) / nch0;
     const int nch = (B + chunk - 1) / chunk;
     const size_t sm = oreduce_tc_smem(c);
-    cudaFuncSetAttribute(oreduce_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     CR_LAUNCH(c, CR_KERNEL_REDUCE,
               oreduce_tc_kernel<<<dim3(nch, (c->N + 127) / 128), RED_THREADS, sm, c->stream>>>(
                   spins, (const cpx<float>*)T, (const cpx<float>*)g, B, c->N, c->M, c->P, chunk,
                   NCp, NT, cols, c->partial, skip, c->d_status));
     *nch_out = nch;
     return cr_check_launch(c, "oreduce_tc_kernel");
+}
+
+// Opt the tensor-core kernels into the shared memory they need; called once
+// per context (not from a hot call, so that hot calls stay capturable).
+cr_status tc_prepare(cr_ctx* c) {
+    if (!tc_supported(c)) return CR_OK;
+    cudaError_t e = cudaFuncSetAttribute(ov_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ov_tc_smem(c));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(oreduce_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)oreduce_tc_smem(c));
+    return e == cudaSuccess ? CR_OK : cr_fail(c, CR_ECUDA, "tc_prepare: %s", cudaGetErrorString(e));
 }

@@ -56,9 +56,15 @@ class SeqConfig:
 
 
 class Sequence:
-    """Device state of one Chebyshev sequence (one probe momentum)."""
+    """Device state of one Chebyshev sequence (one probe momentum).
 
-    def __init__(self, ctx, cfg, psi_params, spins_fit, spins_ref):
+    graphs=True captures one natural-gradient iteration (sweep, target, update,
+    theta refresh) in a CUDA graph per kind of step (n = 1, n = 2, n >= 3) and
+    replays it; the moment's inputs are copied into fixed buffers first and
+    the random stream position lives on the device, so replays reproduce the
+    eager launches exactly."""
+
+    def __init__(self, ctx, cfg, psi_params, spins_fit, spins_ref, graphs=False):
         self.ctx, self.cfg = ctx, cfg
         dev = torch.device("cuda")
         cd = ctx.cdtype
@@ -90,6 +96,18 @@ class Sequence:
         self.rng_ref = api.Philox(cfg.seed_ref, 0)
         self.hprime = (cfg.E0, cfg.a, cfg.Wp)
         self.n_done = 0
+        self.graphs = graphs
+        self.graph_launches = 0
+        if graphs:
+            self.work = torch.zeros(P, dtype=cd, device=dev)
+            self.prev_buf = torch.zeros(P, dtype=cd, device=dev)
+            self.prev2_buf = torch.zeros(P, dtype=cd, device=dev)
+            self.beta_buf = torch.zeros(2, dtype=torch.complex128, device=dev)
+            self.stats_it = torch.zeros(api.STATS_LEN, dtype=torch.float64, device=dev)
+            self.ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+            self.rng_dev = api.Philox(cfg.seed, 0, self.ctr.data_ptr())
+            self._graph = {}
+            self._eager_done = set()
 
     def state(self, n):
         return self.ctx.state(self.params[n], probe=(n == 0), q=self.cfg.q)
@@ -123,25 +141,30 @@ class Sequence:
         c.cheb_local_target(n, self.state(n - 1), prev2, self.betas[n - 1:n], b2, cfg.E0, cfg.a,
                             cfg.Wp, self.spins, self.lp, self.R, mean_out=mean_out)
 
-    def _samples(self, pn, n_sweeps, replay):
+    def _samples(self, pn, n_sweeps, replay, record=None):
         """Fresh samples of |psi_n|^2: Metropolis sweeps, or, when replaying,
         the next recorded configuration set (then theta, log psi and tanh theta
-        are evaluated on it)."""
+        are evaluated on it).  record: list receiving a copy of each sample set."""
         c = self.ctx
         if replay is None:
             c.mc_sweep(pn, self.spins, self.theta, n_sweeps, self.rng, logpsi_out=self.lp,
                        tanh_out=self.tanh)
+            if record is not None:
+                record.append(self.spins.clone())
         else:
             self.spins.copy_(next(replay))
             c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
             c.logderiv(pn, self.spins, self.theta, tanh_out=self.tanh)
 
-    def fit(self, n, replay=None):
+    def fit(self, n, replay=None, record=None):
         """Projection step n: fit RBM_n, then beta_n and mu_n.
 
         replay: optional iterable of walker configurations (device int8
         [B, N]) to use, in order, instead of the sampler: one per iteration
-        and one for beta_n (the recorded samples of another run)."""
+        and one for beta_n (the recorded samples of another run).
+        record: optional list that receives those configurations."""
+        if self.graphs and replay is None and record is None:
+            return self._fit_graph(n)
         c, cfg = self.ctx, self.cfg
         replay = iter(replay) if replay is not None else None
         pn = self.params[n]
@@ -152,15 +175,85 @@ class Sequence:
                 c.mc_sweep(pn, self.spins, self.theta, cfg.n_therm, self.rng, logpsi_out=self.lp,
                            tanh_out=self.tanh)
         for it in range(cfg.n_iter):
-            self._samples(pn, cfg.sweeps_per_iter, replay)
+            self._samples(pn, cfg.sweeps_per_iter, replay, record)
             self._target(n)
             c.sr_step(pn, self.spins, self.tanh, self.R, cfg.dgamma, cfg.shift, solver=cfg.solver,
                       cg_maxit=cfg.cg_maxit, cg_tol=cfg.cg_tol, stats_out=self.stats[n, it],
                       jacobi=cfg.jacobi)
             if replay is None:
                 c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
-        self._samples(pn, cfg.sweeps_per_iter, replay)
+        self._samples(pn, cfg.sweeps_per_iter, replay, record)
         self._target(n, mean_out=self.betas[n:n + 1])
+        self._moment(n)
+        self.n_done = n + 1
+
+    # ------------------------------------------------------------ graphs
+    def counter(self):
+        """Current position of the fit walkers' random stream."""
+        if self.graphs:
+            return int(self.ctr.item())
+        return self.rng.counter
+
+    def _iteration(self, kind):
+        """One natural-gradient iteration on the fixed buffers (capturable)."""
+        c, cfg = self.ctx, self.cfg
+        c.mc_sweep(self.work, self.spins, self.theta, cfg.sweeps_per_iter, self.rng_dev,
+                   logpsi_out=self.lp, tanh_out=self.tanh)
+        self._target_fixed(kind)
+        c.sr_step(self.work, self.spins, self.tanh, self.R, cfg.dgamma, cfg.shift,
+                  solver=cfg.solver, cg_maxit=cfg.cg_maxit, cg_tol=cfg.cg_tol,
+                  stats_out=self.stats_it, jacobi=cfg.jacobi)
+        c.rbm_logpsi(self.work, self.spins, self.theta, self.lp)
+
+    def _target_fixed(self, kind, mean_out=None):
+        c, cfg, q = self.ctx, self.cfg, self.cfg.q
+        prev = c.state(self.prev_buf, probe=(kind == 1), q=q)
+        prev2 = c.state(self.prev2_buf, probe=(kind == 2), q=q) if kind >= 2 else None
+        c.cheb_local_target(1 if kind == 1 else 2, prev, prev2, self.beta_buf[0:1],
+                            self.beta_buf[1:2] if kind >= 2 else None, cfg.E0, cfg.a, cfg.Wp,
+                            self.spins, self.lp, self.R, mean_out=mean_out)
+
+    def _replay(self, kind):
+        if kind not in self._graph:
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            main = torch.cuda.current_stream()
+            side.wait_stream(main)
+            n0 = self.ctx.n_launches()
+            with torch.cuda.graph(g, stream=side):
+                self.ctx.set_stream(side)
+                self._iteration(kind)
+            self.ctx.set_stream(main)
+            main.wait_stream(side)
+            self._graph[kind] = (g, self.ctx.n_launches() - n0)
+        g, nodes = self._graph[kind]
+        g.replay()
+        self.graph_launches += nodes
+
+    def _fit_graph(self, n):
+        c, cfg = self.ctx, self.cfg
+        kind = 1 if n == 1 else (2 if n == 2 else 3)
+        self.work.copy_(self.init1 if n == 1 else self.params[n - 1])
+        self.prev_buf.copy_(self.params[n - 1])
+        self.beta_buf[0:1].copy_(self.betas[n - 1:n])
+        if n >= 2:
+            self.prev2_buf.copy_(self.params[n - 2])
+            self.beta_buf[1:2].copy_(self.betas[n - 2:n - 1])
+        c.rbm_logpsi(self.work, self.spins, self.theta, self.lp)
+        if cfg.n_therm:
+            c.mc_sweep(self.work, self.spins, self.theta, cfg.n_therm, self.rng_dev,
+                       logpsi_out=self.lp, tanh_out=self.tanh)
+        for it in range(cfg.n_iter):
+            if kind in self._eager_done:
+                self._replay(kind)
+            else:
+                self._iteration(kind)  # first of its kind: eager (loads every kernel)
+                self._eager_done.add(kind)
+            self.stats[n, it].copy_(self.stats_it)
+        c.mc_sweep(self.work, self.spins, self.theta, cfg.sweeps_per_iter, self.rng_dev,
+                   logpsi_out=self.lp, tanh_out=self.tanh)
+        self._target_fixed(kind, mean_out=self.betas[n:n + 1])
+        self.params[n].copy_(self.work)
         self._moment(n)
         self.n_done = n + 1
 
