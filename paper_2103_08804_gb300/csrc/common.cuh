@@ -177,7 +177,7 @@ struct cr_ctx {
     void* theta_tmp;         // [maxB][M]
     void* lp_tmp;            // [2][maxB]
     void* u_tmp;             // [maxB]
-    double* partial;         // [n_chunks][P + 2 + M] complex128
+    double* partial;         // [n_chunks][P + 2 + M] complex, context precision
     double* red;             // [3][P + 2 + M] complex128 reduced sums
     double* F;               // [P] complex128
     double* cg;              // x, r, p, Ap, diag: [5][P] complex128

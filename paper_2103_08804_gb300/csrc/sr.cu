@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(128) oreduce2_kernel(const int8_t* __restrict_
             }
         }
     }
-    cpx<double>* out = (cpx<double>*)partial + (size_t)c * (P + 2 + M);
+    // partial rows in the context precision (the sums above are in R)
+    cpx<R>* out = (cpx<R>*)partial + (size_t)c * (P + 2 + M);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int j = j0 + tj + k;
@@ -223,30 +224,32 @@ __global__ void __launch_bounds__(128) oreduce2_kernel(const int8_t* __restrict_
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int i = i0 + ti + a;
-            if (i < N) out[N + M + (size_t)i * M + j] = ccast<double>(acc[a][k]);
+            if (i < N) out[N + M + (size_t)i * M + j] = acc[a][k];
         }
         if (b_cta && ti == 0) {
-            out[N + j] = ccast<double>(accb[k]);
-            if (!CONJ) out[P + 2 + j] = {(double)acct[k], 0.0};
+            out[N + j] = accb[k];
+            if (!CONJ) out[P + 2 + j] = {acct[k], R(0)};
         }
     }
-    if (a_cta && t < TI && i0 + t < N) out[i0 + t] = ccast<double>(acca);
+    if (a_cta && t < TI && i0 + t < N) out[i0 + t] = acca;
     if (a_cta && b_cta && t == 0) {
-        out[P] = ccast<double>(accg);
-        out[P + 1] = {(double)accgg, 0.0};
+        out[P] = accg;
+        out[P + 1] = {accgg, R(0)};
     }
 }
 
-// red[k] = sum over chunks of partial[c][k] (k < len, rows `stride` long), in chunk order.
+// red[k] = sum over chunks of partial[c][k] (k < len, rows `stride` long of
+// cpx<RP>), in chunk order, in float64.
+template <typename RP>
 __global__ void combine_kernel(const double* __restrict__ partial, int n_chunks, int len,
                                int stride, double* __restrict__ red,
                                const double* __restrict__ skip) {
     if (skip && *skip != 0.0) return;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= len) return;
-    const cpx<double>* p = (const cpx<double>*)partial;
+    const cpx<RP>* p = (const cpx<RP>*)partial;
     cpx<double> s = {0.0, 0.0};
-    for (int c = 0; c < n_chunks; ++c) s = s + p[(size_t)c * stride + k];
+    for (int c = 0; c < n_chunks; ++c) s = s + ccast<double>(p[(size_t)c * stride + k]);
     ((cpx<double>*)red)[k] = s;
 }
 
@@ -266,7 +269,7 @@ static cr_status oreduce_t(cr_ctx* c, const int8_t* spins, const void* T, const 
     if (s != CR_OK) return s;
     if (!red_out) return CR_OK;  // the caller combines the chunk rows itself
     const int len = CONJ ? P + 2 : P + 2 + M;
-    CR_LAUNCH(c, CR_K_OTHER, combine_kernel<<<(len + 255) / 256, 256, 0, c->stream>>>(
+    CR_LAUNCH(c, CR_K_OTHER, combine_kernel<R><<<(len + 255) / 256, 256, 0, c->stream>>>(
                                  c->partial, nch, len, P + 2 + M, red_out, skip));
     return cr_check_launch(c, "combine_kernel");
 }
@@ -515,6 +518,7 @@ __device__ double sum_parts(const double* p, int n, double* red) {
 // order (a fixed summation order, so the result is deterministic).
 constexpr int CGA_K = 32;
 
+template <typename RP>
 __global__ void __launch_bounds__(256) cg_apply_kernel(const double* __restrict__ partial,
                                                        int nch, int stride,
                                                        const double* __restrict__ redO_, int P,
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(256) cg_apply_kernel(const double* __restrict_
     if (scal[2] != 0.0) return;
     __shared__ cpx<double> grp[8][CGA_K];
     __shared__ cpx<double> smu;
-    const cpx<double>* pt = (const cpx<double>*)partial;
+    const cpx<RP>* pt = (const cpx<RP>*)partial;
     const cpx<double>* sO = (const cpx<double>*)redO_;
     cpx<double>* p = (cpx<double>*)cg_ + 2 * P;
     cpx<double>* Ap = (cpx<double>*)cg_ + 3 * P;
@@ -533,11 +537,11 @@ __global__ void __launch_bounds__(256) cg_apply_kernel(const double* __restrict_
     const int k = blockIdx.x * CGA_K + lane;
     cpx<double> w = {0.0, 0.0};
     if (k < P)
-        for (int c = wid; c < nch; c += 8) w = w + pt[(size_t)c * stride + k];
+        for (int c = wid; c < nch; c += 8) w = w + ccast<double>(pt[(size_t)c * stride + k]);
     grp[wid][lane] = w;
     if (wid == 7) {
         cpx<double> su = {0.0, 0.0};
-        for (int c = lane; c < nch; c += 32) su = su + pt[(size_t)c * stride + P];
+        for (int c = lane; c < nch; c += 32) su = su + ccast<double>(pt[(size_t)c * stride + P]);
         su = warp_sum(su);
         if (lane == 0) smu = su;
     }
@@ -691,7 +695,7 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
                 s = oreduce(c, true, spins, T, c->u_tmp, B, nullptr, done);
             }
             if (s != CR_OK) return s;
-            CR_LAUNCH(c, CR_KERNEL_CG, cg_apply_kernel<<<napp, 256, 0, c->stream>>>(
+            CR_LAUNCH(c, CR_KERNEL_CG, cg_apply_kernel<R><<<napp, 256, 0, c->stream>>>(
                                            c->partial, nch, P + 2 + c->M, redO, P, B, o->shift,
                                            c->cg, c->cgpart, c->scal));
             CR_LAUNCH(c, CR_KERNEL_CG, cg_xr_kernel<<<nblk, CG_TPB, 0, c->stream>>>(
@@ -805,8 +809,8 @@ static cudaError_t noalloc_backward_t(int N, int M, const int8_t* spins, const v
         if (dbl) LAUNCH(4, 2); else LAUNCH(4, 4);
     }
 #undef LAUNCH
-    combine_kernel<<<(P + 2 + 255) / 256, 256, 0, st>>>(scratch, nch, P + 2, P + 2 + M, red,
-                                                         nullptr);
+    combine_kernel<double><<<(P + 2 + 255) / 256, 256, 0, st>>>(scratch, nch, P + 2, P + 2 + M,
+                                                                 red, nullptr);
     to_params_kernel<R><<<(P + 255) / 256, 256, 0, st>>>(red, P, (cpx<R>*)grad);
     return cudaGetLastError();
 }

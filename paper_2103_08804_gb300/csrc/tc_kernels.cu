@@ -351,12 +351,12 @@ __global__ void __launch_bounds__(RED_THREADS, 1) oreduce_tc_kernel(
     red[hh * 128 + r] = acca;
     red[256 + hh * 128 + r] = accb[0];
     __syncthreads();
-    cpx<double>* out = (cpx<double>*)partial + (size_t)c * (P + 2 + M);
+    cpx<float>* out = (cpx<float>*)partial + (size_t)c * (P + 2 + M);  // float32 rows
     if (hh == 0) {
-        if (i < N) out[i] = ccast<double>(red[r] + red[128 + r]);
+        if (i < N) out[i] = red[r] + red[128 + r];
         if (blockIdx.y == 0) {
             const int j = r;
-            if (j < M) out[N + j] = ccast<double>(red[256 + r] + red[384 + r]);
+            if (j < M) out[N + j] = red[256 + r] + red[384 + r];
         }
     }
     __syncthreads();
@@ -364,11 +364,11 @@ __global__ void __launch_bounds__(RED_THREADS, 1) oreduce_tc_kernel(
         red[hh * 128 + r] = accb[1];
         __syncthreads();
         if (hh == 0 && blockIdx.y == 0 && 128 + r < M)
-            out[N + 128 + r] = ccast<double>(red[r] + red[128 + r]);
+            out[N + 128 + r] = red[r] + red[128 + r];
     }
     if (blockIdx.y == 0 && t == 0) {
-        out[P] = ccast<double>(accg);
-        out[P + 1] = {(double)accgg, 0.0};
+        out[P] = accg;
+        out[P + 1] = {accgg, 0.f};
     }
     // D rows: warps w and w + 4 read the same TMEM lanes, each half of the columns
     const int lb = warp & 3, half = warp >> 2, row = 32 * lb + lane, ir = i0 + row;
@@ -380,8 +380,7 @@ __global__ void __launch_bounds__(RED_THREADS, 1) oreduce_tc_kernel(
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int j = nt * 128 + ch * 8 + q;
-                if (ir < N && j < M)
-                    out[N + M + (size_t)ir * M + j] = {(double)d[2 * q], (double)d[2 * q + 1]};
+                if (ir < N && j < M) out[N + M + (size_t)ir * M + j] = {d[2 * q], d[2 * q + 1]};
             }
         }
     if (!ok && t == 0) set_status(status, CR_ETIMEOUT);
