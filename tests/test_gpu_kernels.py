@@ -329,6 +329,42 @@ def test_gram_and_krylov_on_exact_vectors():
     assert np.allclose(host(wts), wk[np.argsort(lam)], atol=1e-9 * abs(mu_ex[0]))
 
 
+@pytest.mark.parametrize("Nm", [40, 100, 300])
+def test_krylov_against_oracle_at_scale(Nm):
+    """cheb_krylov on a well-conditioned Gram pair of Nm states (random states,
+    G = X^dag X / D, H = X^dag A X / D with spec(A) in [-W', W']): poles,
+    weights and corrected moments equal the oracle's, and the weights sum to
+    mu'_0 = G_00."""
+    from oracle import krylov
+    rng = np.random.default_rng(60 + Nm)
+    D = 3 * Nm
+    X = (rng.standard_normal((D, Nm)) + 1j * rng.standard_normal((D, Nm))) / np.sqrt(2)
+    A = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+    A = (A + A.conj().T) / 2
+    e = np.linalg.eigvalsh(A)
+    A = (A - e[0] * np.eye(D)) / ((e[-1] - e[0]) / 1.975) - 0.9875 * np.eye(D)
+    G = X.conj().T @ X / D
+    H = X.conj().T @ A @ X / D
+    H = (H + H.conj().T) / 2
+    n_out = 2 * Nm if Nm <= 100 else 64
+    ctx = _ctx(4, 1, 4, 8, 0)
+    mu = torch.zeros(n_out, dtype=torch.complex128, device="cuda")
+    poles = torch.zeros(Nm, dtype=torch.float64, device="cuda")
+    wts = torch.zeros(Nm, dtype=torch.float64, device="cuda")
+    rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.cheb_krylov(dev(G, torch.complex128), dev(H, torch.complex128), 1e-12, n_out, mu, poles,
+                    wts, rank)
+    ctx.sync_status()
+    assert int(host(rank)[0]) == Nm
+    lam_ref, w_ref = krylov.krylov_poles(G, H, cutoff=1e-12)
+    order = np.argsort(lam_ref)
+    assert np.allclose(host(poles), lam_ref[order], atol=1e-9)
+    assert np.allclose(host(wts), w_ref[order], atol=1e-9 * abs(G[0, 0]))
+    mc = krylov.corrected_moments(G, H, n_out, cutoff=1e-12)
+    assert np.allclose(host(mu), mc, atol=1e-8 * abs(G[0, 0]))
+    assert abs(np.sum(host(wts)) - G[0, 0].real) < 1e-9 * abs(G[0, 0])
+
+
 def test_zero_walkers_is_a_no_op():
     from paper_2103_08804_gb300 import api
     ctx = _ctx(8, 1, 8, 16, 1)
