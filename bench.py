@@ -9,6 +9,13 @@ then beta_n = <R> and mu_n with its Krylov columns.  Inputs are synthetic
 L2 is flushed between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload chain64|batch]
+
+--workload batch times the momentum scan instead: all 15 irreducible momenta
+of an 8 x 8 square lattice (q = 0 has a vanishing probe and is skipped) plus
+chains of 48 and 96 sites at q = pi/2, alpha = 2, 8192 walkers each; one step
+= one moment of every sequence, with every sequence's iteration in one CUDA
+graph (chunk counts autotuned), against one sequence after another.
 
 Prints one JSON line.  Under torchrun every rank runs an independent
 sequence (a different seed): weak scaling with no data-path collective.
@@ -49,6 +56,7 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying CUDA graphs")
     ap.add_argument("--cpu-walkers", type=int, default=2048)
+    ap.add_argument("--workload", default="chain64", choices=["chain64", "batch"])
     return ap.parse_args()
 
 
@@ -470,9 +478,172 @@ def run_reference(args):
     }), flush=True)
 
 
+def roofline_reduce(ctx, seq, wl, clocks, n_eager=3):
+    """Live CUDA-event timing of the O-reduction on eagerly launched
+    iterations of the current step (graph replays do not re-record host-side
+    events), as a roofline entry of the context's path."""
+    import torch
+
+    from paper_2103_08804_gb300 import api
+    ctx.time_kernel("reduce", 4096)
+    for _ in range(n_eager):
+        seq._iteration(3)
+    torch.cuda.synchronize()
+    ktimes = ctx.kernel_times()
+    ctx.time_kernel(None, 1)
+    k_ms = float(np.mean(ktimes)) if ktimes else None
+    f_sm = clocks.get("sm_mhz") or 2070.0
+    peaks, peak_src = measured_peaks()
+    if ctx.prec == api.MIXED:
+        peak = float(peaks["hbm_gbs"])
+        achieved = reduce_bytes(wl) / (k_ms * 1e-3) / 1e9 if k_ms else None
+        roof = {"kernel": "oreduce_tc_kernel (tcgen05 bf16x3, split-K over walkers)",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "work_per_launch": reduce_bytes(wl),
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+    else:
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_sm * 1e6 / 1e12
+        achieved = reduce_flops(wl) / (k_ms * 1e-3) / 1e12 if k_ms else None
+        roof = {"kernel": "oreduce2_kernel (sum_s sigma_si conj(T_sj) g_s, FP32 FMA)",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "work_per_launch": reduce_flops(wl),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}
+    roof.update({"frac": (achieved / peak) if achieved else None, "traffic": None,
+                 "launches_timed": len(ktimes), "avg_launch_ms": k_ms})
+    return roof
+
+
+def run_batch(args):
+    """Momentum scan: every sequence advances one moment per step."""
+    import torch
+
+    from paper_2103_08804_gb300 import api, batch, synth
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    K, W = args.steps, args.warmup
+    n_moments = 1 + W + 3 * K
+    iters = 50 if args.iters is None else args.iters
+    specs = batch.momentum_scan_specs(L=8, alpha=2, chains=(48, 96), walkers=8192,
+                                      n_moments=n_moments, n_iter=iters, sigma=0.02,
+                                      seed=1000 + 17 * rank, n_therm=2, n_therm_ref=20,
+                                      solver=api.SOLVE_CG, cg_maxit=args.cg_maxit,
+                                      cg_tol=args.cg_tol, jacobi=args.jacobi)
+    main = torch.cuda.Stream()
+    torch.cuda.set_stream(main)
+    t0 = time.perf_counter()
+    b = batch.Batch(specs, prec=api.MIXED, tune=True)
+    tune_s = time.perf_counter() - t0
+    n_seq = len(b.seqs)
+    b.start()
+    for n in range(1, 1 + W):
+        b.fit(n)
+    for c in b.ctxs:
+        c.sync_status()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_batch_r{rank}.csv")
+                if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_batch_r{rank}.csv")
+    res = {}
+    n = 1 + W
+    with ClockSampler(clk_path, local) as clk:
+        for schedule in ("batched", "per_q"):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(K)]
+            barrier(ws)
+            torch.cuda.synchronize()
+            l0 = sum(c.n_launches() for c in b.ctxs) + b.graph_launches
+            for k in range(K):
+                flush.zero_()
+                ev[k][0].record(main)
+                b.fit(n, schedule=schedule)
+                ev[k][1].record(main)
+                n += 1
+            torch.cuda.synchronize()
+            barrier(ws)
+            ms = max_over_ranks(ws, float(np.mean([e[0].elapsed_time(e[1]) for e in ev])))
+            launches = sum(c.n_launches() for c in b.ctxs) + b.graph_launches - l0
+            res[schedule] = {"ms_per_step": ms, "value": ws * n_seq * 3600.0 * 1000.0 / ms,
+                             "gpu_launches": int(launches)}
+    clocks = clk.summary()
+    for c in b.ctxs:
+        c.sync_status()
+    # end to end: every sequence's inputs from pinned host buffers, results back
+    seqs = b.seqs
+    h_in = [(torch.empty(2, s.ctx.P, dtype=s.ctx.cdtype).pin_memory(),
+             torch.empty(2, dtype=torch.complex128).pin_memory(),
+             torch.empty_like(s.spins, device="cpu").pin_memory()) for s in seqs]
+    h_out = [(torch.empty(s.ctx.P, dtype=s.ctx.cdtype).pin_memory(),
+              torch.empty(2, dtype=torch.complex128).pin_memory()) for s in seqs]
+    e2e_ms = []
+    for k in range(K):
+        m = n + k
+        for s, (hp, hb, hs) in zip(seqs, h_in):
+            hp.copy_(s.params[m - 2:m])
+            hb.copy_(s.betas[m - 2:m])
+            hs.copy_(s.spins)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        for s, (hp, hb, hs) in zip(seqs, h_in):
+            s.params[m - 2:m].copy_(hp, non_blocking=True)
+            s.betas[m - 2:m].copy_(hb, non_blocking=True)
+            s.spins.copy_(hs, non_blocking=True)
+        b.fit(m)
+        for s, (ho, hr) in zip(seqs, h_out):
+            ho.copy_(s.params[m], non_blocking=True)
+            hr[0:1].copy_(s.betas[m:m + 1], non_blocking=True)
+            hr[1:2].copy_(s.mu[m:m + 1], non_blocking=True)
+        e1.record(main)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_v = max_over_ranks(ws, float(np.mean(e2e_ms)))
+    Bi = sum(hp.numel() * hp.element_size() + 32 + hs.numel() for hp, _, hs in h_in)
+    Bo = sum(ho.numel() * ho.element_size() + 32 for ho, _ in h_out)
+    sq = next(i for i, s in enumerate(b.active) if s.cfg.Ly > 1)
+    b._fork()
+    with torch.cuda.stream(b.streams[sq]):
+        roof = roofline_reduce(b.ctxs[sq], seqs[sq], synth.WORKLOADS["square8"], clocks)
+    b._join()
+    for c in b.ctxs:
+        c.sync_status()
+    bt, pq = res["batched"], res["per_q"]
+    out = {
+        "metric": "Chebyshev moments/hour", "value": bt["value"], "unit": "moments/hour",
+        "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": bt["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: bf16x3 tensor-core contractions with f32 accumulation, f32 elsewhere, "
+                 "f64 sums and CG",
+        "data": "synthetic (random complex RBMs, sigma=0.02; seeded S^z=0 walkers)",
+        "config": {"workload": "momentum scan: 8x8 square lattice at its 15 irreducible q "
+                               "(q=0 skipped: vanishing probe) + chains N=48 and N=96 at q=pi/2, "
+                               "alpha=2, 8192 walkers each, one moment of every sequence per step",
+                   "sequences": n_seq, "skipped": b.skipped, "iters_per_moment": iters,
+                   "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol,
+                   "chunks": dict(zip([s.name for s in b.active], b.chunks)),
+                   "autotune_s": tune_s, "l2": "256 MiB buffer written between timed steps",
+                   "launch": "one CUDA graph per iteration holding every sequence (forked streams)",
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": bt["gpu_launches"],
+        "clocks": clocks,
+        "e2e": {"value": ws * n_seq * 3600.0 * 1000.0 / e2e_v, "unit": "moments/hour",
+                "h2d_bytes_per_step": Bi, "d2h_bytes_per_step": Bo},
+        "roofline": roof,
+        "per_q": pq,
+        "batched_over_per_q": bt["value"] / pq["value"],
+    }
+    del flush
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_batch(a)
     else:
         run_ours(a)

@@ -153,6 +153,15 @@ cr_status cr_create(cr_ctx** out, const cr_lattice* lattice, int M, int max_walk
 cr_status cr_destroy(cr_ctx* ctx);
 /* Rebind the context to another stream (e.g. a graph-capture stream). */
 cr_status cr_set_stream(cr_ctx* ctx, void* stream);
+/* Walker chunks of the split-K reductions (the sums over walkers in F, the
+   O averages and O^dag u are formed per chunk, then combined in float64 in
+   chunk order).  cr_create picks ceil(max_walkers / 128), at most 128, which
+   is also the largest value cr_set_chunks accepts (cr_max_chunks).  Fewer
+   chunks launch fewer CTAs, which pays when several contexts run
+   concurrently on one GPU; the results change only by the summation order.
+   Returns CR_EINVAL outside [1, cr_max_chunks]. */
+cr_status cr_set_chunks(cr_ctx* ctx, int n_chunks);
+int cr_max_chunks(const cr_ctx* ctx);
 /* Text of the last error of this context (static storage in the context). */
 const char* cr_last_error(const cr_ctx* ctx);
 /* Synchronise the context stream, then read and clear the device status

@@ -26,7 +26,7 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds", "rbm_logpsi", "mc_sweep",
            "cheb_local_target", "logderiv", "logpsi_backward", "sr_step", "cheb_moment",
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
-           "logpsi_backward_noalloc")
+           "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5}
 
 
@@ -92,10 +92,12 @@ def load(path=None):
     lib.cr_n_launches.restype = ctypes.c_longlong
     lib.cr_time_kernel.argtypes = [vp, i, i]
     lib.cr_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
+    lib.cr_set_chunks.argtypes = [vp, i]
+    lib.cr_max_chunks.argtypes = [vp]
     lib.logpsi_backward_noalloc.argtypes = [i, i, i, vp, vp, i, vp, vp, vp, ctypes.c_char_p, i]
     for f in SYMBOLS:
         if f not in ("cr_last_error", "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds",
-                     "cr_n_launches"):
+                     "cr_n_launches", "cr_max_chunks"):
             getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -154,6 +156,13 @@ class Context:
         self._stream = stream
         self._check(self.lib.cr_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)),
                     "cr_set_stream")
+
+    def set_chunks(self, n_chunks):
+        """Walker chunks of the split-K reductions (1 .. max_chunks())."""
+        self._check(self.lib.cr_set_chunks(self.h, int(n_chunks)), "cr_set_chunks")
+
+    def max_chunks(self):
+        return int(self.lib.cr_max_chunks(self.h))
 
     def sync_status(self):
         self._check(self.lib.cr_sync_status(self.h), "device status")

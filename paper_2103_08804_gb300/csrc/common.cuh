@@ -166,7 +166,8 @@ struct cr_ctx {
     double J;
     cr_prec prec;
     int max_walkers, flags;
-    int n_chunks;            // walker chunks of the reductions
+    int n_chunks;            // walker chunks of the reductions (<= max_chunks)
+    int max_chunks;          // chunks the partial-row workspace holds
     int n_sm;                // multiprocessors of the device
     cudaStream_t stream;
     char err[512];

@@ -122,6 +122,7 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
     // at least 128 walkers; partial rows cost (P + 2 + M) x 16 bytes each
     c->n_chunks = (max_walkers + 127) / 128;
     if (c->n_chunks > 128) c->n_chunks = 128;
+    c->max_chunks = c->n_chunks;
     if (c->N > 1024 || c->N % 2) {
         free(c);
         return CR_EINVAL;
@@ -198,6 +199,16 @@ extern "C" cr_status cr_set_stream(cr_ctx* c, void* stream) {
     c->stream = (cudaStream_t)stream;
     return CR_OK;
 }
+
+extern "C" cr_status cr_set_chunks(cr_ctx* c, int n_chunks) {
+    if (!c) return CR_EINVAL;
+    if (n_chunks < 1 || n_chunks > c->max_chunks)
+        return cr_fail(c, CR_EINVAL, "n_chunks %d outside [1, %d]", n_chunks, c->max_chunks);
+    c->n_chunks = n_chunks;
+    return CR_OK;
+}
+
+extern "C" int cr_max_chunks(const cr_ctx* c) { return c ? c->max_chunks : -1; }
 
 extern "C" const char* cr_last_error(const cr_ctx* c) { return c ? c->err : "null context"; }
 

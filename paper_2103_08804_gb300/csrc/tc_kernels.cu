@@ -414,9 +414,15 @@ size_t oreduce_tc_smem(const cr_ctx* c) {
 
 // Whether the tensor-core kernels cover this context (M <= 256 and the
 // operands fit in shared memory); otherwise the float32 kernels run.
+// Shared-memory bound of the tensor-core kernels.  The kernels' opt-in limit
+// is set to this bound, not to one context's need: the attribute belongs to
+// the function, so a context created later with a smaller need must not
+// lower it under an earlier context's launches.
+constexpr int TC_SMEM_LIMIT = 200 * 1024;
+
 bool tc_supported(const cr_ctx* c) {
-    return c->prec == CR_MIXED && c->M <= 256 && ov_tc_smem(c) <= 200 * 1024 &&
-           oreduce_tc_smem(c) <= 200 * 1024;
+    return c->prec == CR_MIXED && c->M <= 256 && ov_tc_smem(c) <= TC_SMEM_LIMIT &&
+           oreduce_tc_smem(c) <= TC_SMEM_LIMIT;
 }
 
 cr_status launch_ov_tc(cr_ctx* c, const void* v, const int8_t* spins, int B, const void* T,
@@ -457,9 +463,9 @@ cr_status launch_oreduce_tc(cr_ctx* c, const int8_t* spins, const void* T, const
 cr_status tc_prepare(cr_ctx* c) {
     if (!tc_supported(c)) return CR_OK;
     cudaError_t e = cudaFuncSetAttribute(ov_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ov_tc_smem(c));
+                                         TC_SMEM_LIMIT);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(oreduce_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)oreduce_tc_smem(c));
+                                 TC_SMEM_LIMIT);
     return e == cudaSuccess ? CR_OK : cr_fail(c, CR_ECUDA, "tc_prepare: %s", cudaGetErrorString(e));
 }

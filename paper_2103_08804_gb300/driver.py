@@ -230,9 +230,15 @@ class Sequence:
         g.replay()
         self.graph_launches += nodes
 
-    def _fit_graph(self, n):
+    @staticmethod
+    def kind_of(n):
+        """Graph kind of projection step n: the target's form differs for
+        n = 1 (probe state), n = 2 (probe as t~_{n-2}) and n >= 3."""
+        return 1 if n == 1 else (2 if n == 2 else 3)
+
+    def _moment_begin(self, n):
+        """Inputs of step n into the fixed buffers, theta and thermalisation."""
         c, cfg = self.ctx, self.cfg
-        kind = 1 if n == 1 else (2 if n == 2 else 3)
         self.work.copy_(self.init1 if n == 1 else self.params[n - 1])
         self.prev_buf.copy_(self.params[n - 1])
         self.beta_buf[0:1].copy_(self.betas[n - 1:n])
@@ -243,19 +249,28 @@ class Sequence:
         if cfg.n_therm:
             c.mc_sweep(self.work, self.spins, self.theta, cfg.n_therm, self.rng_dev,
                        logpsi_out=self.lp, tanh_out=self.tanh)
-        for it in range(cfg.n_iter):
+
+    def _moment_end(self, n):
+        """Fresh samples, beta_n = <R>, the parameters of RBM_n and mu_n."""
+        c, cfg = self.ctx, self.cfg
+        c.mc_sweep(self.work, self.spins, self.theta, cfg.sweeps_per_iter, self.rng_dev,
+                   logpsi_out=self.lp, tanh_out=self.tanh)
+        self._target_fixed(self.kind_of(n), mean_out=self.betas[n:n + 1])
+        self.params[n].copy_(self.work)
+        self._moment(n)
+        self.n_done = n + 1
+
+    def _fit_graph(self, n):
+        kind = self.kind_of(n)
+        self._moment_begin(n)
+        for it in range(self.cfg.n_iter):
             if kind in self._eager_done:
                 self._replay(kind)
             else:
                 self._iteration(kind)  # first of its kind: eager (loads every kernel)
                 self._eager_done.add(kind)
             self.stats[n, it].copy_(self.stats_it)
-        c.mc_sweep(self.work, self.spins, self.theta, cfg.sweeps_per_iter, self.rng_dev,
-                   logpsi_out=self.lp, tanh_out=self.tanh)
-        self._target_fixed(kind, mean_out=self.betas[n:n + 1])
-        self.params[n].copy_(self.work)
-        self._moment(n)
-        self.n_done = n + 1
+        self._moment_end(n)
 
     def run(self, n_moments=None):
         nm = self.cfg.n_moments if n_moments is None else n_moments
