@@ -9,13 +9,19 @@ then beta_n = <R> and mu_n with its Krylov columns.  Inputs are synthetic
 L2 is flushed between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload chain64|batch]
+                  [--workload chain64|batch|square10]
 
 --workload batch times the momentum scan instead: all 15 irreducible momenta
 of an 8 x 8 square lattice (q = 0 has a vanishing probe and is skipped) plus
 chains of 48 and 96 sites at q = pi/2, alpha = 2, 8192 walkers each; one step
 = one moment of every sequence, with every sequence's iteration in one CUDA
 graph (chunk counts autotuned), against one sequence after another.
+
+--workload square10 times the explicit-S path: 10 x 10 square lattice,
+alpha = 1 (P = 10,200), 32768 walkers, q = (pi, pi); S built on the tensor
+cores (three-term bf16 splits), blocked Cholesky in float32 refined in
+float64; it also reports |S_mixed - S_fp64|_F / |S_fp64|_F on a walker
+sample, for the default splits and for the cheaper two-term (bf16x3) form.
 
 Prints one JSON line.  Under torchrun every rank runs an independent
 sequence (a different seed): weak scaling with no data-path collective.
@@ -56,7 +62,9 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying CUDA graphs")
     ap.add_argument("--cpu-walkers", type=int, default=2048)
-    ap.add_argument("--workload", default="chain64", choices=["chain64", "batch"])
+    ap.add_argument("--workload", default="chain64", choices=["chain64", "batch", "square10"])
+    ap.add_argument("--s-error-walkers", type=int, default=2048,
+                    help="square10: walkers of the tensor-core S vs float64 S comparison")
     return ap.parse_args()
 
 
@@ -146,13 +154,16 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def make_config(wl, E0, a, args, n_moments, seed):
+def make_config(wl, E0, a, args, n_moments, seed, solver=None):
     from paper_2103_08804_gb300 import api, driver
     return driver.SeqConfig(Lx=wl.Lx, Ly=wl.Ly, M=wl.M, q=wl.q, n_moments=n_moments,
-                            n_iter=wl.iters if args.iters is None else args.iters, shift=wl.shift, dgamma=wl.dgamma, E0=E0, a=a,
+                            n_iter=wl.iters if args.iters is None else args.iters,
+                            shift=wl.shift, dgamma=wl.dgamma, E0=E0, a=a,
                             Wp=0.9875, n_therm=2, sweeps_per_iter=1, n_therm_ref=20, seed=seed,
-                            seed_ref=seed + 1, solver=api.SOLVE_CG, cg_maxit=args.cg_maxit,
-                            cg_tol=args.cg_tol, jacobi=args.jacobi, krylov=True)
+                            seed_ref=seed + 1,
+                            solver=api.SOLVE_CG if solver is None else solver,
+                            cg_maxit=args.cg_maxit, cg_tol=args.cg_tol, jacobi=args.jacobi,
+                            krylov=True)
 
 
 def reduce_flops(wl):
@@ -513,6 +524,144 @@ def roofline_reduce(ctx, seq, wl, clocks, n_eager=3):
     return roof
 
 
+def run_explicit(args):
+    """Explicit-S workload: one step = one moment with the Cholesky solve."""
+    import torch
+
+    from paper_2103_08804_gb300 import api, driver, synth
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    wl = synth.WORKLOADS["square10"]
+    E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
+    K, W = args.steps, args.warmup
+    n_moments = 1 + W + 2 * K
+    seed = 2000 + 17 * rank
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(wl.Lx, wl.Ly, wl.M, wl.walkers, prec=api.MIXED, explicit_s=True,
+                      stream=stream)
+    cfg = make_config(wl, E0, a, args, n_moments, seed, solver=api.SOLVE_CHOLESKY)
+    psi = synth.rbm_params(seed, wl.N, wl.M, wl.sigma)
+    seq = driver.Sequence(ctx, cfg, psi, synth.sz0_spins(seed + 2, wl.walkers, wl.N),
+                          synth.sz0_spins(seed + 3, wl.walkers, wl.N), graphs=not args.eager)
+    seq.start()
+    for n in range(1, 1 + W):
+        seq.fit(n)
+    ctx.sync_status()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches0 = ctx.n_launches() + seq.graph_launches
+    clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_square10_r{rank}.csv")
+                if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                else f"/tmp/clocks_square10_r{rank}.csv")
+    with ClockSampler(clk_path, local) as clk:
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            seq.fit(1 + W + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = ctx.n_launches() + seq.graph_launches - launches0
+    ms = max_over_ranks(ws, float(np.mean([e[0].elapsed_time(e[1]) for e in ev])))
+    clocks = clk.summary()
+    st = seq.stats[1 + W:1 + W + K].cpu().numpy()
+    # live kernel times on eager iterations of the same step: the Gram kernel,
+    # and the whole natural-gradient update (S, factor, refined solve)
+    if args.eager:
+        raise SystemExit("--workload square10 times its kernels on the graph-mode buffers")
+    ctx.time_kernel("sbuild", 64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n_eager = 2
+    for _ in range(n_eager):
+        seq._iteration(3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gram_ms = float(np.mean(ctx.kernel_times()))
+    iter_ms = e0.elapsed_time(e1) / n_eager
+    ctx.time_kernel("chol", 20000)
+    seq._iteration(3)
+    torch.cuda.synchronize()
+    chol_ms = float(np.sum(ctx.kernel_times()))
+    ctx.time_kernel(None, 1)
+    ctx.sync_status()
+    # tensor-core S against a float64 context on a walker sample
+    Bs = min(args.s_error_walkers, wl.walkers)
+    ref = api.Context(wl.Lx, wl.Ly, wl.M, Bs, prec=api.FP64, explicit_s=True, stream=stream)
+    sp = seq.spins[:Bs].contiguous()
+    th = torch.empty(Bs, wl.M, dtype=torch.complex128, device="cuda")
+    p_last = seq.params[W + K].to(torch.complex128)
+    ref.rbm_logpsi(p_last, sp, th)
+    T64 = torch.empty_like(th)
+    ref.logderiv(p_last, sp, th, tanh_out=T64)
+    S64 = ref.sr_smatrix(sp, T64, wl.shift)
+    nrm = torch.linalg.norm(S64)
+    S32 = ctx.sr_smatrix(sp, T64.to(torch.complex64), wl.shift)
+    ctx.sync_status()
+    s_err = float(torch.linalg.norm(S32 - S64) / nrm)
+    del S32
+    x3 = api.Context(wl.Lx, wl.Ly, wl.M, Bs, prec=api.MIXED, explicit_s=True, stream=stream,
+                     s_bf16x3=True)
+    S32 = x3.sr_smatrix(sp, T64.to(torch.complex64), wl.shift)
+    x3.sync_status()
+    ref.sync_status()
+    s_err_x3 = float(torch.linalg.norm(S32 - S64) / nrm)
+    del S64, S32, ref, x3
+    P, B = wl.P, wl.walkers
+    flops = 8.0 * P * (P + 1) / 2 * B          # Hermitian half of O^dag O, complex MACs x 8
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
+    achieved = flops / (gram_ms * 1e-3) / 1e12
+    roof = {"kernel": "sgram_tc_kernel<3> (tcgen05, three-term bf16 splits: six bf16 "
+                      "products per float32 product, float32 accumulation in TMEM)",
+            "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "work_per_launch": flops,
+            "avg_launch_ms": gram_ms,
+            "peak_source": f"MEASURED_PEAKS.json bf16_tflops_sustained ({peak_src}); six bf16 "
+                           f"products per product, so frac <= 1/6"}
+    sweeps_per_moment = cfg.n_therm + cfg.n_iter * cfg.sweeps_per_iter + cfg.sweeps_per_iter
+    e2e_ms, Bi, Bo = e2e(seq, ctx, 1 + W + K, K, stream)
+    e2e_ms = max_over_ranks(ws, e2e_ms)
+    out = {
+        "metric": "Chebyshev moments/hour", "value": ws * 3600.0 * 1000.0 / ms,
+        "unit": "moments/hour", "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: S on tensor cores from three-term bf16 splits (six products, f32 "
+                 "accumulation), f32 Cholesky factor, f64 refinement, f32 elsewhere",
+        "data": "synthetic (random complex RBM, sigma=0.01; seeded S^z=0 walkers)",
+        "config": {"workload": "square10: periodic 10x10 Heisenberg lattice, RBM alpha=1 (M=100, "
+                               "P=10200), 32768 walkers, q=(pi,pi), explicit S + Cholesky",
+                   "iters_per_moment": cfg.n_iter, "l2": "256 MiB buffer written between timed steps",
+                   "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
+                   "parallelism": f"replicas x{ws}"},
+        "mc_samples_per_s": ws * wl.walkers * sweeps_per_moment / (ms * 1e-3),
+        "gpu_launches": int(launches), "clocks": clocks,
+        "e2e": {"value": ws * 3600.0 * 1000.0 / e2e_ms, "unit": "moments/hour",
+                "h2d_bytes_per_step": Bi, "d2h_bytes_per_step": Bo},
+        "roofline": roof,
+        "s_rel_error_vs_fp64": s_err,
+        "s_rel_error_vs_fp64_bf16x3": s_err_x3,
+        "s_error_sample": f"{Bs} walkers of the fit set, RBM of the last fitted moment",
+        "iteration_ms": iter_ms, "sbuild_ms": gram_ms,
+        "cholesky_ms": chol_ms,
+        "cholesky_note": "blocked factor (potrf, trsm, syrk) plus the triangular solves of "
+                         "every refinement step, summed over one iteration",
+        "refine_steps_mean": float(st[..., 5].mean()),
+        "refine_residual_max": float(st[..., 6].max()),
+    }
+    del flush
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_batch(args):
     """Momentum scan: every sequence advances one moment per step."""
     import torch
@@ -645,5 +794,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "batch":
         run_batch(a)
+    elif a.workload == "square10":
+        run_explicit(a)
     else:
         run_ours(a)

@@ -83,9 +83,26 @@ typedef enum {
 /* Context flags. */
 #define CR_CTX_EXPLICIT_S 1 /* allocate the explicit P x P complex128 S for
                                Cholesky solves */
+#define CR_CTX_S_BF16X3 2   /* mixed contexts: build the explicit S from two-term
+                               bf16 splits (three products, about 2^-16 relative
+                               per product) instead of the default three-term
+                               splits (six products, about float32 accuracy).
+                               Cheaper, but its error can make S + shift I
+                               indefinite at small shifts (CR_ESINGULAR). */
 
 /* Solvers for sr_step. */
-#define CR_SOLVE_CHOLESKY 0 /* explicit S, float64 Cholesky (needs CR_CTX_EXPLICIT_S) */
+#define CR_SOLVE_CHOLESKY 0 /* explicit S and a direct solve (needs CR_CTX_EXPLICIT_S):
+                               float64 contexts with P <= 2048 factor S in float64 in one
+                               CTA; every other context factors S blocked (64 x 64
+                               blocks, many CTAs) in the factor precision (float64 for
+                               float64 contexts, float32 otherwise) and refines the
+                               solution in float64 against S until |r| <= 1e-12 |F|,
+                               the residual stops halving, or min(cg_maxit, 10) steps
+                               (stats [5] steps, [6] relative residual).  Mixed
+                               contexts build S on the tensor cores (bf16 splits of
+                               both operands, float32 accumulation; see
+                               CR_CTX_S_BF16X3); the others accumulate it in
+                               float64. */
 #define CR_SOLVE_CG 1       /* matrix-free S v = O^dag (O v) / Ns, float64 CG */
 
 /* Length of the stats array written by sr_step (complex128 / float64 slots). */
@@ -180,6 +197,8 @@ cr_status cr_sync_status(cr_ctx* ctx);
 #define CR_KERNEL_OV 3      /* u = O v (matrix-free S, first half) */
 #define CR_KERNEL_REDUCE 4  /* sum_s op(O_k(s)) g_s (F, Obar, S v second half, VJP) */
 #define CR_KERNEL_CG 5      /* CG vector update */
+#define CR_KERNEL_SBUILD 6  /* explicit S: Gram matrix of O */
+#define CR_KERNEL_CHOL 7    /* blocked Cholesky factor and triangular solves */
 long long cr_n_launches(const cr_ctx* ctx);
 cr_status cr_time_kernel(cr_ctx* ctx, int kernel_id, int capacity);
 int cr_kernel_times(cr_ctx* ctx, float* ms_out, int capacity);
@@ -277,6 +296,14 @@ cr_status logpsi_backward_noalloc(int N, int M, cr_prec prec, const int8_t* spin
    [CR_STATS_LEN] (device) or NULL. */
 cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, const void* tanh_theta,
                   const void* R, int B, const cr_sr_opts* opts, double* stats_out);
+
+/* Sec. III: the explicit S + shift I of sr_step's Cholesky path, built by
+   the same kernels on samples of |psi|^2 (Obar from the same samples), copied
+   to S_out: device complex128 [P][P], the full Hermitian matrix.  For
+   inspection and accuracy checks (mixed contexts: the tensor-core S against
+   a float64 context's).  Needs CR_CTX_EXPLICIT_S. */
+cr_status sr_smatrix(cr_ctx* ctx, const int8_t* spins, const void* tanh_theta, int B,
+                     double shift, double* S_out);
 
 /* Secs. II and IV, on samples s of |psi|^2 of the reference state psi:
      Bcol[s]  = beta t~(s) / psi(s)              (B_n of the Gram estimator)

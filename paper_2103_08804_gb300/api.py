@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libchebrbm.so")
 FP64, FP32, MIXED = 0, 1, 2
 SOLVE_CHOLESKY, SOLVE_CG = 0, 1
 CTX_EXPLICIT_S = 1
+CTX_S_BF16X3 = 2
 STATS_LEN = 8
 STATUS = {0: "CR_OK", 1: "CR_EINVAL", 2: "CR_ENOMEM", 3: "CR_ECUDA", 4: "CR_ETIMEOUT",
           5: "CR_ENOTCONV", 6: "CR_ESINGULAR", 7: "CR_ENONFINITE"}
@@ -26,8 +27,9 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds", "rbm_logpsi", "mc_sweep",
            "cheb_local_target", "logderiv", "logpsi_backward", "sr_step", "cheb_moment",
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
-           "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks")
-KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5}
+           "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix")
+KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
+          "chol": 7}
 
 
 class Lattice(ctypes.Structure):
@@ -93,6 +95,7 @@ def load(path=None):
     lib.cr_time_kernel.argtypes = [vp, i, i]
     lib.cr_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     lib.cr_set_chunks.argtypes = [vp, i]
+    lib.sr_smatrix.argtypes = [vp, vp, vp, i, d, vp]
     lib.cr_max_chunks.argtypes = [vp]
     lib.logpsi_backward_noalloc.argtypes = [i, i, i, vp, vp, i, vp, vp, vp, ctypes.c_char_p, i]
     for f in SYMBOLS:
@@ -114,7 +117,8 @@ def _ptr(t):
 class Context:
     """One lattice, one hidden width, one precision; owns the library context."""
 
-    def __init__(self, Lx, Ly, M, max_walkers, prec=FP32, explicit_s=False, J=1.0, stream=None):
+    def __init__(self, Lx, Ly, M, max_walkers, prec=FP32, explicit_s=False, J=1.0, stream=None,
+                 s_bf16x3=False):
         if not torch.cuda.is_available():
             raise RuntimeError("libchebrbm needs a CUDA device")
         self.lib = load()
@@ -128,7 +132,8 @@ class Context:
         h = ctypes.c_void_p()
         lat = Lattice(Lx, Ly, J)
         s = self.lib.cr_create(ctypes.byref(h), ctypes.byref(lat), M, max_walkers, prec,
-                               CTX_EXPLICIT_S if explicit_s else 0, ctypes.c_void_p(st.cuda_stream))
+                               (CTX_EXPLICIT_S if explicit_s else 0) |
+                               (CTX_S_BF16X3 if s_bf16x3 else 0), ctypes.c_void_p(st.cuda_stream))
         if s != 0:
             raise CRError(f"cr_create failed: {STATUS.get(s, s)}")
         self.h = h
@@ -289,6 +294,19 @@ class Context:
         o = SROpts(dgamma, shift, solver, cg_maxit, cg_tol, 1 if jacobi else 0)
         self._check(self.lib.sr_step(self.h, _ptr(params), _ptr(spins), _ptr(tanh_theta), _ptr(R),
                                      B, ctypes.byref(o), _ptr(stats_out)), "sr_step")
+
+    def sr_smatrix(self, spins, tanh_theta, shift, S_out=None):
+        """Explicit S + shift I (complex128 [P, P]) as built by the Cholesky path."""
+        B = self._spins(spins)
+        self._c(tanh_theta, (B, self.M), "tanh_theta")
+        if S_out is None:
+            S_out = torch.empty(self.P, self.P, dtype=torch.complex128, device=spins.device)
+        if not (S_out.dtype == torch.complex128 and S_out.is_cuda and S_out.is_contiguous()
+                and tuple(S_out.shape) == (self.P, self.P)):
+            raise ValueError("S_out: need a contiguous CUDA complex128 [P, P] tensor")
+        self._check(self.lib.sr_smatrix(self.h, _ptr(spins), _ptr(tanh_theta), B, float(shift),
+                                        _ptr(S_out)), "sr_smatrix")
+        return S_out
 
     def cheb_moment(self, state, beta, q, spins, logpsi_ref, hprime=None, Bcol=None, HBcol=None,
                     mu_out=None):

@@ -190,6 +190,10 @@ struct cr_ctx {
     void* O_tmp;             // [maxB][P] context precision (explicit S only)
     double* kry;             // Krylov workspace
     size_t kry_len;
+    void* Lf;                // [P][P] Cholesky factor, factor precision (blocked path only)
+    unsigned char* Xt;       // bf16 hi/lo planes of X^T (mixed explicit S only)
+    int2* gtiles;            // lower-triangle blocks of G (mixed explicit S only)
+    int n_gtiles;
     long long n_launches;    // kernels launched so far
     cr_ktimer kt;
 };
@@ -211,6 +215,19 @@ void cr_kt_end(cr_ctx* c);
     } while (0)
 #define CR_K_OTHER (-2)
 cr_status cr_check_launch(cr_ctx* c, const char* what);
+
+// Explicit S and the direct solve (chol.cu, tc_kernels.cu).  Float64
+// contexts up to CHOL_SMALL_P parameters keep the single-CTA float64
+// Cholesky; every other explicit-S context takes the blocked path.
+#define CHOL_SMALL_P 2048
+bool chol_blocked(const cr_ctx* c);
+size_t chol_factor_bytes(const cr_ctx* c);
+size_t chol_cgpart_len();
+cr_status chol_factor(cr_ctx* c);
+cr_status chol_refine_solve(cr_ctx* c, const double* F, int maxit);
+cr_status launch_sbuild_tc(cr_ctx* c, const int8_t* spins, const void* T, int B,
+                           const double* redO, double shift);
+void launch_smirror(cr_ctx* c);  // S[k][l] = conj(S[l][k]) for k < l
 
 // Tables for a state (rbm.cu).
 cr_status build_tables(cr_ctx* c, const void* params, int slot);

@@ -7,6 +7,8 @@
 #include "common.cuh"
 
 cr_status tc_prepare(cr_ctx* c);
+void sgram_geometry(const cr_ctx* c, int* R2, int* nkc_max, size_t* plane_bytes, int* npl);
+std::vector<int2> sgram_tiles(int P);
 
 cr_status cr_fail(cr_ctx* c, cr_status s, const char* fmt, ...) {
     if (c) {
@@ -150,11 +152,25 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
     ALLOC(c->F, P * 16);
     ALLOC(c->cg, 5 * P * 16);
     ALLOC(c->p_lo, P * cs);
-    ALLOC(c->cgpart, ((P + 31) / 32 + 2 * ((P + 255) / 256)) * sizeof(double));
+    size_t ncgpart = (P + 31) / 32 + 2 * ((P + 255) / 256);
+    if (ncgpart < chol_cgpart_len()) ncgpart = chol_cgpart_len();
+    ALLOC(c->cgpart, ncgpart * sizeof(double));
     ALLOC(c->scal, 64 * sizeof(double));
+    std::vector<int2> gt;
     if (flags & CR_CTX_EXPLICIT_S) {
         ALLOC(c->S, P * P * 16);
-        ALLOC(c->O_tmp, B * P * cs);
+        if (prec == CR_MIXED) {
+            int R2, nkc, npl;
+            size_t pb;
+            sgram_geometry(c, &R2, &nkc, &pb, &npl);
+            gt = sgram_tiles(c->P);
+            c->n_gtiles = (int)gt.size();
+            ALLOC(c->Xt, npl * pb);
+            ALLOC(c->gtiles, gt.size() * sizeof(int2));
+        } else {
+            ALLOC(c->O_tmp, B * P * cs);
+        }
+        if (chol_blocked(c)) ALLOC(c->Lf, chol_factor_bytes(c));
     }
 #undef ALLOC
     if (e != cudaSuccess) {
@@ -167,6 +183,8 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
         cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
     std::vector<int2> bonds = make_bonds(c->Lx, c->Ly);
     e = cudaMemcpy(c->d_bonds, bonds.data(), Nb * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !gt.empty())
+        e = cudaMemcpy(c->gtiles, gt.data(), gt.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, 64 * sizeof(double));
     if (e != cudaSuccess || tc_prepare(c) != CR_OK) {
@@ -181,7 +199,8 @@ extern "C" cr_status cr_destroy(cr_ctx* c) {
     if (!c) return CR_EINVAL;
     kt_free(c);
     void* ptrs[] = {c->d_status, c->d_bonds, c->theta_tmp, c->lp_tmp, c->u_tmp, c->partial,
-                    c->red, c->F, c->cg, c->p_lo, c->cgpart, c->scal, c->S, c->O_tmp, c->kry};
+                    c->red, c->F, c->cg, c->p_lo, c->cgpart, c->scal, c->S, c->O_tmp, c->kry,
+                    c->Lf, c->Xt, c->gtiles};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int s = 0; s < 2; ++s) {

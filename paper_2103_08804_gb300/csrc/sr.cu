@@ -650,6 +650,27 @@ __global__ void fnorm_kernel(const double* __restrict__ F_, int P, double* __res
     if (threadIdx.x == 0) scal[1] = s;
 }
 
+// S + shift I into c->S (full Hermitian, float64; the upper triangle a
+// mirror of the lower): tensor cores (bf16x3) for mixed contexts; otherwise
+// O materialised in the context precision and its Gram matrix accumulated
+// in float64.
+template <typename R>
+static cr_status build_s(cr_ctx* c, const int8_t* spins, const void* T, int B,
+                         const double* redO, double shift) {
+    if (c->prec == CR_MIXED) return launch_sbuild_tc(c, spins, T, B, redO, shift);
+    const int P = c->P;
+    const size_t n = (size_t)B * P;
+    CR_LAUNCH(c, CR_K_OTHER,
+              o_from_tanh_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+                  spins, (const cpx<R>*)T, B, c->N, c->M, P, (cpx<R>*)c->O_tmp));
+    dim3 g((P + 15) / 16, (P + 15) / 16);
+    CR_LAUNCH(c, CR_KERNEL_SBUILD,
+              sbuild_kernel<R><<<g, dim3(16, 16), 0, c->stream>>>((const cpx<R>*)c->O_tmp, B, P,
+                                                                  redO, shift, c->S));
+    launch_smirror(c);  // exactly Hermitian off the diagonal
+    return cr_check_launch(c, "explicit S");
+}
+
 template <typename R>
 static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const void* T,
                            const void* Rv, int B, const cr_sr_opts* o, double* stats) {
@@ -664,16 +685,17 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
                                                           c->d_status));
     if ((s = cr_check_launch(c, "force_kernel")) != CR_OK) return s;
     double* x = c->cg;
+    const bool blocked = o->solver == CR_SOLVE_CHOLESKY && chol_blocked(c);
     if (o->solver == CR_SOLVE_CHOLESKY) {
-        size_t n = (size_t)B * P;
-        CR_LAUNCH(c, CR_K_OTHER, o_from_tanh_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
-            spins, (const cpx<R>*)T, B, c->N, c->M, P, (cpx<R>*)c->O_tmp));
-        dim3 g((P + 15) / 16, (P + 15) / 16);
-        CR_LAUNCH(c, CR_K_OTHER, sbuild_kernel<R><<<g, dim3(16, 16), 0, c->stream>>>((const cpx<R>*)c->O_tmp, B, P, redO,
-                                                            o->shift, c->S));
-        CR_LAUNCH(c, CR_K_OTHER, chol_solve_kernel<<<1, 1024, 0, c->stream>>>(c->S, P, c->F, x, c->d_status));
-        CR_LAUNCH(c, CR_K_OTHER, fnorm_kernel<<<1, 1024, 0, c->stream>>>(c->F, P, c->scal));
-        if ((s = cr_check_launch(c, "cholesky path")) != CR_OK) return s;
+        if ((s = build_s<R>(c, spins, T, B, redO, o->shift)) != CR_OK) return s;
+        if (blocked) {
+            if ((s = chol_factor(c)) != CR_OK) return s;
+            if ((s = chol_refine_solve(c, c->F, o->cg_maxit)) != CR_OK) return s;
+        } else {
+            CR_LAUNCH(c, CR_K_OTHER, chol_solve_kernel<<<1, 1024, 0, c->stream>>>(c->S, P, c->F, x, c->d_status));
+            CR_LAUNCH(c, CR_K_OTHER, fnorm_kernel<<<1, 1024, 0, c->stream>>>(c->F, P, c->scal));
+            if ((s = cr_check_launch(c, "cholesky path")) != CR_OK) return s;
+        }
     } else {
         CR_LAUNCH(c, CR_K_OTHER, cg_init_kernel<R><<<1, 1024, 0, c->stream>>>(
                                      c->F, redO, c->N, c->M, P, B, o->shift, o->cg_precond,
@@ -707,7 +729,7 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
         }
     }
     CR_LAUNCH(c, CR_K_OTHER, apply_update_kernel<R><<<(P + 255) / 256, 256, 0, c->stream>>>(
-        (cpx<R>*)params, x, P, c->scal, stats, c->F, c->d_status, o->solver == CR_SOLVE_CG));
+        (cpx<R>*)params, x, P, c->scal, stats, c->F, c->d_status, o->solver == CR_SOLVE_CG || blocked));
     return cr_check_launch(c, "apply_update");
 }
 
@@ -729,6 +751,31 @@ extern "C" cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, con
     return ctx->prec == CR_FP64
                ? sr_step_t<double>(ctx, params, spins, tanh_theta, R, B, opts, stats_out)
                : sr_step_t<float>(ctx, params, spins, tanh_theta, R, B, opts, stats_out);
+}
+
+template <typename R>
+static cr_status smatrix_t(cr_ctx* c, const int8_t* spins, const void* T, int B, double shift,
+                           double* S_out) {
+    double* redO = c->red + 2 * (c->P + 2 + c->M);
+    cr_status s = oreduce(c, false, spins, T, nullptr, B, redO, nullptr);
+    if (s != CR_OK) return s;
+    if ((s = build_s<R>(c, spins, T, B, redO, shift)) != CR_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(S_out, c->S, (size_t)c->P * c->P * 16,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    return e == cudaSuccess ? CR_OK : cr_fail(c, CR_ECUDA, "sr_smatrix copy: %s", cudaGetErrorString(e));
+}
+
+extern "C" cr_status sr_smatrix(cr_ctx* ctx, const int8_t* spins, const void* tanh_theta, int B,
+                                double shift, double* S_out) {
+    if (!ctx) return CR_EINVAL;
+    CR_CHECK_ARG(ctx->flags & CR_CTX_EXPLICIT_S,
+                 "sr_smatrix: needs a context created with CR_CTX_EXPLICIT_S");
+    CR_CHECK_ARG(B >= 1 && B <= ctx->max_walkers, "sr_smatrix: B=%d outside [1, %d]", B,
+                 ctx->max_walkers);
+    CR_CHECK_ARG(spins && tanh_theta && S_out, "sr_smatrix: null array");
+    CR_CHECK_ARG(shift >= 0.0, "sr_smatrix: shift must be >= 0");
+    return ctx->prec == CR_FP64 ? smatrix_t<double>(ctx, spins, tanh_theta, B, shift, S_out)
+                                : smatrix_t<float>(ctx, spins, tanh_theta, B, shift, S_out);
 }
 
 // ------------------------------------------------------ backward of log psi

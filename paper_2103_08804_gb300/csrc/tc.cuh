@@ -91,6 +91,27 @@ CR_D void mbar_init(uint64_t* mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count)
                  : "memory");
 }
+// Arm mbar for one arrival (this thread) plus `bytes` of asynchronous copies.
+CR_D void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile(
+        "{\n"
+        ".reg .b64 st;\n"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n"
+        "}\n" ::"r"(smem_u32(mbar)),
+        "r"(bytes)
+        : "memory");
+}
+
+// Bulk (non-tensor) copy global -> shared, completion counted on mbar in
+// bytes.  Both addresses 16-byte aligned, size a multiple of 16.
+CR_D void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
 CR_D void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
 
 // Wait for the phase with the given parity to complete, giving up after

@@ -14,6 +14,8 @@
 //                     the a-, b- and scalar sums of oreduce_kernel's partial rows
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -27,6 +29,16 @@ CR_D void split3(float x, __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* 
     *mid = __float2bfloat16_rn(r1);
     const float r2 = r1 - __bfloat162float(*mid);
     *lo = __float2bfloat16_rn(r2);
+}
+
+// (hi, lo) += x with hi + lo kept to about twice float32 precision: Knuth's
+// TwoSum gives the rounding error of hi + x exactly, which lo collects.
+CR_D void two_sum_add(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
 }
 
 CR_D uint4 pack8(const __nv_bfloat16* v) {
@@ -389,6 +401,312 @@ __global__ void __launch_bounds__(RED_THREADS, 1) oreduce_tc_kernel(
     if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)tmem_cols);
 }
 
+// ------------------------------------------------- explicit S (Sec. III)
+//
+// S_kl = sum_s conj(O_sk) O_sl / B - conj(Obar_k) Obar_l (+ shift on the
+// diagonal) through the real Gram matrix G = X^T X of X = [Re O | Im O]
+// (column 2k = Re O_k, 2k + 1 = Im O_k):
+//   Re S_kl = G[2k][2l] + G[2k+1][2l+1],  Im S_kl = G[2k][2l+1] - G[2k+1][2l].
+// Both operands are float32 values split into NPL bf16 terms, the products
+// summed in float32 in TMEM over all walkers:
+//   NPL = 3 (default): x = hi + mid + lo, six products hi.hi + hi.mid +
+//     mid.hi + hi.lo + mid.mid + lo.hi, about float32 accuracy ("bf16x6");
+//   NPL = 2 (CR_CTX_S_BF16X3): x = hi + lo + O(2^-17 |x|), three products
+//     hi.hi + hi.lo + lo.hi ("bf16x3").  Its error, about 2^-16 relative per
+//     product, can push the smallest eigenvalues of S + lambda I below
+//     lambda and, at lambda = 1e-3 on large lattices, below zero.
+//
+// TMEM accumulates in float32 with a per-step error that grows with the
+// number of MMAs added into one accumulator (measured: relative ~1e-8 per
+// accumulation), so a 128 x 256 tile of G is accumulated over chunks of CH
+// walkers in one TMEM half while the other half, holding the previous chunk,
+// is added into a compensated float32 accumulator (hi + lo pairs, TwoSum) in
+// shared memory: float64-like sums on the float32 pipe (the float64 pipe of
+// this GPU is far too narrow to keep up with the tensor cores).
+//
+// xt_prep_kernel writes X^T as NPL bf16 planes, each an array of tiles
+// [row block of 128 G rows][walker chunk of KC] in the K-major no-swizzle
+// core-matrix layout, so one bulk copy moves one tile.
+// sgram_tc_kernel: persistent, 160 threads.  Warp 0 (one thread) copies
+// operand tiles through two stages and issues the MMAs of chunk c into TMEM
+// columns [256 (c % 2), +256); warps 1-4 (TMEM lanes 32 (w % 4) .. +31) wait
+// for the chunk, add it to the compensated tile of S (64 x 128 entries, formed
+// from adjacent lanes = rows 2k, 2k + 1), release the TMEM half, and at the
+// end of a tile write S and clear the accumulator.
+template <int NPL>
+struct SGram {
+    static constexpr int KC = NPL == 2 ? 32 : 16;    // walkers per operand tile
+    static constexpr int TILE = 128 * KC * 2;         // bytes of one 128-row tile
+    static constexpr int NSTG = 2;                    // pipeline stages
+    static constexpr int STAGE = NPL * 3 * TILE;      // A (1 row block) + B (2), NPL planes
+    static constexpr int NPROD = NPL == 2 ? 3 : 6;
+    static constexpr int CH = NPL == 2 ? 256 : 128;   // walkers per TMEM accumulation
+    static constexpr int ACC_LD = 129;                // padded row of the accumulator tile
+    static constexpr size_t ACC_BYTES = (size_t)64 * ACC_LD * 16;
+    static constexpr size_t SMEM = (size_t)NSTG * STAGE + ACC_BYTES + 128;
+    // planes (A, B) of product pr: (hi, hi), (hi, mid), (mid, hi), (hi, lo),
+    // (mid, mid), (lo, hi); NPL = 2 takes the first three (mid = lo there)
+    static CR_HD int pa(int pr) {
+        constexpr int v[6] = {0, 0, 1, 0, 1, 2};
+        return v[pr];
+    }
+    static CR_HD int pb(int pr) {
+        constexpr int v[6] = {0, 1, 0, 2, 1, 0};
+        return v[pr];
+    }
+};
+constexpr int GR_THREADS = 160;
+
+template <int NPL>
+__global__ void xt_prep_kernel(const int8_t* __restrict__ spins, const cpx<float>* __restrict__ T,
+                               int B, int N, int M, int P, int R2, int nkc_max, int nkc,
+                               size_t plane_bytes, unsigned char* __restrict__ Xt) {
+    using G = SGram<NPL>;
+    constexpr int NG = G::KC / 8;  // groups of 8 walkers per tile
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)R2 * nkc * NG;
+    if (idx >= total) return;
+    const int r = (int)(idx % 128), grp = (int)((idx / 128) % NG);
+    const size_t rest = idx / (128 * NG);
+    const int kc = (int)(rest % nkc), rb = (int)(rest / nkc);
+    const int row = rb * 128 + r, k = row >> 1, im = row & 1;
+    __nv_bfloat16 t0[8], t1[8], t2[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int s = kc * G::KC + grp * 8 + q;
+        float x = 0.f;
+        if (k < P && s < B) {
+            cpx<float> o;
+            if (k < N) {
+                o = {(float)spins[(size_t)s * N + k], 0.f};
+            } else if (k < N + M) {
+                o = T[(size_t)s * M + (k - N)];
+            } else {
+                const int i = (k - N - M) / M, j = (k - N - M) % M;
+                o = (float)spins[(size_t)s * N + i] * T[(size_t)s * M + j];
+            }
+            x = im ? o.y : o.x;
+        }
+        if (NPL == 3) {
+            split3(x, &t0[q], &t1[q], &t2[q]);
+        } else {
+            t0[q] = __float2bfloat16_rn(x);
+            t1[q] = __float2bfloat16_rn(x - __bfloat162float(t0[q]));
+        }
+    }
+    const size_t off =
+        ((size_t)rb * nkc_max + kc) * G::TILE + tc::kmajor_offset(r, grp * 8, G::KC);
+    *reinterpret_cast<uint4*>(Xt + off) = pack8(t0);
+    *reinterpret_cast<uint4*>(Xt + plane_bytes + off) = pack8(t1);
+    if (NPL == 3) *reinterpret_cast<uint4*>(Xt + 2 * plane_bytes + off) = pack8(t2);
+}
+
+template <int NPL>
+__global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
+    const unsigned char* __restrict__ Xt, size_t plane_bytes, int nkc_max, int nkc,
+    const int2* __restrict__ tiles, int ntiles, int P, int B, const double* __restrict__ redO_,
+    double shift, double* __restrict__ S_, int* __restrict__ status) {
+    using G = SGram<NPL>;
+    constexpr int NSTG = G::NSTG, TILE = G::TILE, KPC = G::CH / G::KC;  // tiles per chunk
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float4* acc = (float4*)(sm + NSTG * G::STAGE);  // [64][ACC_LD] (Re hi, Re lo, Im hi, Im lo)
+    uint64_t* full = (uint64_t*)(sm + NSTG * G::STAGE + G::ACC_BYTES);
+    uint64_t* empty = full + NSTG;      // [NSTG] MMAs reading a stage done
+    uint64_t* cdone = full + 2 * NSTG;  // [2] MMAs of a chunk done (per TMEM half)
+    uint64_t* drained = cdone + 2;      // [2] TMEM half read by the 128 drain threads
+    uint32_t* slot = (uint32_t*)(drained + 2);
+    volatile int* abort = (volatile int*)(slot + 1);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (t == 0) {
+        for (int i = 0; i < 2 * NSTG + 2; ++i) tc::mbar_init(&full[i], 1);
+        tc::mbar_init(&drained[0], 128);
+        tc::mbar_init(&drained[1], 128);
+        tc::fence_mbar_init();
+        *abort = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(slot, 512u);
+        tc::tmem_relinquish();
+    }
+    for (int e = t; e < 64 * G::ACC_LD; e += GR_THREADS) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = *slot;
+    const int nchunk = (nkc + KPC - 1) / KPC;
+    // a bounded wait that also gives up once the other role has aborted
+    auto wait = [&](uint64_t* bar, uint32_t par) {
+        for (int i = 0; i < 64; ++i) {
+            if (tc::mbar_wait(bar, par, WAIT_LIMIT >> 6)) return true;
+            if (*abort) return false;
+        }
+        *abort = 1;
+        return false;
+    };
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------------------------------------- producer / MMA issuer
+            const uint32_t idesc = tc::make_idesc_bf16(128, 256);
+            uint32_t gs = 0, gc = 0;  // stages and chunks issued so far (all tiles)
+            uint32_t pend = 0, pend_par = 0;
+            int last_g = -1;          // last stage whose MMAs were committed
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int rt = tiles[tile].x, ct = tiles[tile].y;
+                const uint32_t gs0 = gs;
+                // copy the operands of stage gs0 + kc; its buffer was last read by
+                // the MMAs of stage gs0 + kc - NSTG (possibly of the previous tile)
+                auto load = [&](int kc) {
+                    const uint32_t g = gs0 + kc, b = g % NSTG;
+                    if (g >= NSTG && !wait(&empty[b], ((g - NSTG) / NSTG) & 1)) return false;
+                    pend |= 1u << b;
+                    pend_par = (pend_par & ~(1u << b)) | (((g / NSTG) & 1u) << b);
+                    unsigned char* st = sm + (size_t)b * G::STAGE;
+                    tc::mbar_expect_tx(&full[b], (uint32_t)G::STAGE);
+                    for (int pl = 0; pl < NPL; ++pl) {
+                        const unsigned char* src = Xt + (size_t)pl * plane_bytes;
+                        tc::bulk_g2s(st + pl * TILE, src + ((size_t)rt * nkc_max + kc) * TILE,
+                                     TILE, &full[b]);
+                        for (int q = 0; q < 2; ++q)
+                            tc::bulk_g2s(st + NPL * TILE + (pl * 2 + q) * TILE,
+                                         src + ((size_t)(2 * ct + q) * nkc_max + kc) * TILE, TILE,
+                                         &full[b]);
+                    }
+                    return true;
+                };
+                if (!load(0)) ok = false;
+                for (int kc = 0; kc < nkc && ok; ++kc) {
+                    const uint32_t g = gs0 + kc, b = g % NSTG;
+                    const int ck = kc / KPC, first = (kc % KPC) == 0;
+                    const uint32_t h = (gc + ck) & 1;
+                    // the TMEM half of chunk gc + ck was last used by chunk gc + ck - 2
+                    if (first && gc + ck >= 2 && !wait(&drained[h], ((gc + ck - 2) >> 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    if (!wait(&full[b], (g / NSTG) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    pend &= ~(1u << b);
+                    tc::fence_after_sync();
+                    const unsigned char* st = sm + (size_t)b * G::STAGE;
+                    const uint32_t a0 = tc::smem_u32(st), b0 = tc::smem_u32(st + NPL * TILE);
+#pragma unroll
+                    for (int ks = 0; ks < G::KC / 16; ++ks) {
+#pragma unroll
+                        for (int pr = 0; pr < G::NPROD; ++pr) {
+                            const uint64_t ad = tc::make_desc(
+                                a0 + G::pa(pr) * TILE + ks * 256, 128, 16 * G::KC);
+                            const uint64_t bd = tc::make_desc(
+                                b0 + G::pb(pr) * 2 * TILE + ks * 256, 128, 16 * G::KC);
+                            tc::mma_bf16(taddr + h * 256, ad, bd, idesc,
+                                         !(first && ks == 0 && pr == 0));
+                        }
+                    }
+                    tc::commit(&empty[b]);
+                    last_g = (int)g;
+                    if ((kc + 1) % KPC == 0 || kc + 1 == nkc) tc::commit(&cdone[h]);
+                    if (kc + 1 < nkc && !load(kc + 1)) ok = false;
+                }
+                gs += nkc;
+                gc += nchunk;
+            }
+            if (!ok) {
+                *abort = 1;
+                set_status(status, CR_ETIMEOUT);
+                // let copies in flight land and issued MMAs finish (bounded)
+                for (int b = 0; b < NSTG; ++b)
+                    if (pend & (1u << b)) tc::mbar_wait(&full[b], (pend_par >> b) & 1u, WAIT_LIMIT);
+                if (last_g >= 0)
+                    tc::mbar_wait(&empty[last_g % NSTG], (uint32_t)(last_g / NSTG) & 1u, WAIT_LIMIT);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------- drain (warps 1-4)
+        const int row = 32 * (warp & 3) + lane, odd = lane & 1, kl = row >> 1;
+        const cpx<double>* redO = (const cpx<double>*)redO_;
+        cpx<double>* S = (cpx<double>*)S_;
+        const double inv = 1.0 / B;
+        const int d = t - 32;  // 0 .. 127
+        uint32_t gc = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int rt = tiles[tile].x, ct = tiles[tile].y;
+            for (int ck = 0; ck < nchunk; ++ck, ++gc) {
+                const uint32_t h = gc & 1;
+                // warp-uniform outcome: tcgen05.ld below is a warp-wide instruction
+                if (!__all_sync(0xffffffffu, wait(&cdone[h], (gc >> 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                float4* arow = acc + (size_t)kl * G::ACC_LD + 4 * odd;
+                for (int ch = 0; ch < 16; ++ch) {
+                    float v[16], p[16];
+                    tc::tmem_ld16(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + h * 256 + ch * 16,
+                                  v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) p[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        // even lane: row 2k is its own (v), row 2k+1 the partner's (p); odd: swapped
+                        const float e0 = odd ? p[8 + 2 * q] : v[2 * q];
+                        const float e1 = odd ? p[9 + 2 * q] : v[2 * q + 1];
+                        const float o0 = odd ? v[8 + 2 * q] : p[2 * q];
+                        const float o1 = odd ? v[9 + 2 * q] : p[2 * q + 1];
+                        float4& a = arow[8 * ch + q];
+                        two_sum_add(a.x, a.y, __fadd_rn(e0, o1));
+                        two_sum_add(a.z, a.w, __fsub_rn(e1, o0));
+                    }
+                }
+                tc::fence_before_sync();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(
+                                 tc::smem_u32(&drained[h]))
+                             : "memory");
+            }
+            if (!ok) break;
+            // tile done: S = acc / B - conj(Obar_k) Obar_l (+ shift), then clear
+            asm volatile("bar.sync 1, 128;\n" ::: "memory");
+            for (int e = d; e < 64 * 128; e += 128) {
+                const int i = e >> 7, j = e & 127, k = 64 * rt + i, l = 128 * ct + j;
+                float4& a = acc[(size_t)i * G::ACC_LD + j];
+                if (k < P && l < P) {
+                    const cpx<double> g = {(double)a.x + (double)a.y, (double)a.z + (double)a.w};
+                    cpx<double> val = inv * g - conj(inv * redO[k]) * (inv * redO[l]);
+                    if (k == l) val.x += shift;
+                    S[(size_t)k * P + l] = val;
+                }
+                a = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            asm volatile("bar.sync 1, 128;\n" ::: "memory");
+        }
+        if (!ok && d == 0) set_status(status, CR_ETIMEOUT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 512u);
+}
+
+// S[k][l] = conj(S[l][k]) for k < l (32 x 32 tiles through shared memory).
+__global__ void smirror_kernel(double* __restrict__ S_, int P) {
+    __shared__ cpx<double> tl[32][33];
+    const int bx = blockIdx.x, by = blockIdx.y;  // tile column, tile row
+    if (bx < by) return;                         // tiles on or above the diagonal only
+    cpx<double>* S = (cpx<double>*)S_;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int j = ty; j < 32; j += 8) {
+        const int r = bx * 32 + j, c = by * 32 + tx;  // source: lower block (row bx, col by)
+        if (r < P && c < P) tl[j][tx] = S[(size_t)r * P + c];
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int r = by * 32 + j, c = bx * 32 + tx;  // destination (row by, col bx)
+        if (r < P && c < P && r < c) S[(size_t)r * P + c] = conj(tl[tx][j]);
+    }
+}
+
 // ------------------------------------------------------------ launchers
 
 static int tc_geometry(int M, int* NCp, int* NT) {
@@ -458,9 +776,79 @@ cr_status launch_oreduce_tc(cr_ctx* c, const int8_t* spins, const void* T, const
     return cr_check_launch(c, "oreduce_tc_kernel");
 }
 
+static int sgram_npl(const cr_ctx* c) { return (c->flags & CR_CTX_S_BF16X3) ? 2 : 3; }
+
+template <int NPL> size_t sgram_smem_t() { return SGram<NPL>::SMEM; }
+
+// Operand planes of the explicit-S Gram kernel: rows of G padded to a
+// multiple of 512, walkers to a multiple of the tile's walker count.
+void sgram_geometry(const cr_ctx* c, int* R2, int* nkc_max, size_t* plane_bytes, int* npl) {
+    *npl = sgram_npl(c);
+    const int kc = *npl == 2 ? SGram<2>::KC : SGram<3>::KC;
+    *R2 = ((2 * c->P + 511) / 512) * 512;
+    *nkc_max = (c->max_walkers + kc - 1) / kc;
+    *plane_bytes = (size_t)(*R2 / 128) * (size_t)(*nkc_max) * (size_t)(128 * kc * 2);
+}
+
+// Lower-triangle blocks of G (128-row block rt, 256-column block ct with
+// 256 ct <= 128 rt + 127), column-block major so that concurrently running
+// CTAs share the column operand in L2.
+std::vector<int2> sgram_tiles(int P) {
+    const int R2 = ((2 * P + 511) / 512) * 512;
+    std::vector<int2> v;
+    for (int ct = 0; ct < R2 / 256; ++ct)
+        for (int rt = 0; rt * 128 < 2 * P; ++rt)
+            if (256 * ct <= 128 * rt + 127) v.push_back(make_int2(rt, ct));
+    return v;
+}
+
+void launch_smirror(cr_ctx* c);
+
+template <int NPL>
+static cr_status sbuild_tc_t(cr_ctx* c, const int8_t* spins, const void* T, int B,
+                             const double* redO, double shift) {
+    int R2, nkc_max, npl;
+    size_t pb;
+    sgram_geometry(c, &R2, &nkc_max, &pb, &npl);
+    constexpr int KC = SGram<NPL>::KC;
+    const int nkc = (B + KC - 1) / KC;
+    const size_t n = (size_t)R2 * nkc * (KC / 8);
+    CR_LAUNCH(c, CR_K_OTHER,
+              xt_prep_kernel<NPL><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+                  spins, (const cpx<float>*)T, B, c->N, c->M, c->P, R2, nkc_max, nkc, pb, c->Xt));
+    const int grid = c->n_gtiles < c->n_sm ? c->n_gtiles : c->n_sm;
+    CR_LAUNCH(c, CR_KERNEL_SBUILD,
+              sgram_tc_kernel<NPL><<<grid, GR_THREADS, sgram_smem_t<NPL>(), c->stream>>>(
+                  c->Xt, pb, nkc_max, nkc, c->gtiles, c->n_gtiles, c->P, B, redO, shift, c->S,
+                  c->d_status));
+    launch_smirror(c);
+    return cr_check_launch(c, "explicit S (tensor cores)");
+}
+
+cr_status launch_sbuild_tc(cr_ctx* c, const int8_t* spins, const void* T, int B,
+                           const double* redO, double shift) {
+    return sgram_npl(c) == 2 ? sbuild_tc_t<2>(c, spins, T, B, redO, shift)
+                             : sbuild_tc_t<3>(c, spins, T, B, redO, shift);
+}
+
+void launch_smirror(cr_ctx* c) {
+    const int nt = (c->P + 31) / 32;
+    CR_LAUNCH(c, CR_K_OTHER, smirror_kernel<<<dim3(nt, nt), dim3(32, 8), 0, c->stream>>>(c->S, c->P));
+}
+
 // Opt the tensor-core kernels into the shared memory they need; called once
 // per context (not from a hot call, so that hot calls stay capturable).
 cr_status tc_prepare(cr_ctx* c) {
+    if (c->prec == CR_MIXED && (c->flags & CR_CTX_EXPLICIT_S)) {
+        cudaError_t e = cudaFuncSetAttribute(sgram_tc_kernel<2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sgram_smem_t<2>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sgram_tc_kernel<3>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sgram_smem_t<3>());
+        if (e != cudaSuccess) return cr_fail(c, CR_ECUDA, "tc_prepare: %s", cudaGetErrorString(e));
+    }
     if (!tc_supported(c)) return CR_OK;
     cudaError_t e = cudaFuncSetAttribute(ov_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          TC_SMEM_LIMIT);
