@@ -588,6 +588,10 @@ def run_explicit(args):
     seq._iteration(3)
     torch.cuda.synchronize()
     chol_ms = float(np.sum(ctx.kernel_times()))
+    ctx.time_kernel("trsv", 20000)
+    seq._iteration(3)
+    torch.cuda.synchronize()
+    trsv_ms = float(np.sum(ctx.kernel_times()))
     ctx.time_kernel(None, 1)
     ctx.sync_status()
     # tensor-core S against a float64 context on a walker sample
@@ -648,9 +652,9 @@ def run_explicit(args):
         "s_rel_error_vs_fp64_bf16x3": s_err_x3,
         "s_error_sample": f"{Bs} walkers of the fit set, RBM of the last fitted moment",
         "iteration_ms": iter_ms, "sbuild_ms": gram_ms,
-        "cholesky_ms": chol_ms,
-        "cholesky_note": "blocked factor (potrf, trsm, syrk) plus the triangular solves of "
-                         "every refinement step, summed over one iteration",
+        "factor_ms": chol_ms, "trsv_ms": trsv_ms,
+        "factor_note": "factor_ms: blocked factor (potrf, trsm, syrk kernels) of one iteration; "
+                       "trsv_ms: the triangular solves of all its refinement steps",
         "refine_steps_mean": float(st[..., 5].mean()),
         "refine_residual_max": float(st[..., 6].max()),
     }

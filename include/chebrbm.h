@@ -198,7 +198,8 @@ cr_status cr_sync_status(cr_ctx* ctx);
 #define CR_KERNEL_REDUCE 4  /* sum_s op(O_k(s)) g_s (F, Obar, S v second half, VJP) */
 #define CR_KERNEL_CG 5      /* CG vector update */
 #define CR_KERNEL_SBUILD 6  /* explicit S: Gram matrix of O */
-#define CR_KERNEL_CHOL 7    /* blocked Cholesky factor and triangular solves */
+#define CR_KERNEL_CHOL 7    /* blocked Cholesky factor (potrf, trsm, syrk) */
+#define CR_KERNEL_TRSV 8    /* triangular solves of the refinement */
 long long cr_n_launches(const cr_ctx* ctx);
 cr_status cr_time_kernel(cr_ctx* ctx, int kernel_id, int capacity);
 int cr_kernel_times(cr_ctx* ctx, float* ms_out, int capacity);

@@ -29,7 +29,7 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
            "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
-          "chol": 7}
+          "chol": 7, "trsv": 8}
 
 
 class Lattice(ctypes.Structure):

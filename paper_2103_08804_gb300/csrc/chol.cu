@@ -6,11 +6,12 @@
 // lower triangle is copied into the factor buffer L in the factor precision
 // (float64 for float64 contexts, float32 otherwise) and factored in place in
 // 64 x 64 blocks.  Per block column J:
-//   potrf_kernel   L_JJ = chol(A_JJ)                   (one CTA, float64 in smem)
+//   potrf_kernel   L_JJ = chol(A_JJ)                   (one CTA, in shared memory)
 //   trsm_kernel    L_IJ = A_IJ L_JJ^{-dag}, I > J      (one warp per row)
 //   syrk_kernel    A_IK -= L_IJ L_KJ^dag, J < K <= I   (one CTA per 64 x 64 block)
-// The solve with a float32 factor is accurate to about kappa * 2^-24, so it
-// is refined in float64 (Wilkinson's iterative refinement):
+// The solve with a float32 factor (and float32 arithmetic in the triangular
+// solves) is accurate to about kappa * 2^-24, so it is refined in float64
+// (Wilkinson's iterative refinement; the residual is formed in float64):
 //   x = 0, r = F;  repeat { d = L^{-dag} L^{-1} r;  x += d;  r = F - S x }
 // until |r| <= REFINE_TOL |F|, the residual stops shrinking (by 2x), or
 // REFINE_MAXIT steps.  A float64 factor needs one step.  The triangular
@@ -40,34 +41,36 @@ __global__ void chol_copy_kernel(const double* __restrict__ S_, int P, cpx<R>* _
     if (idx < (size_t)P * P) L[idx] = ccast<R>(((const cpx<double>*)S_)[idx]);
 }
 
-// Factor the diagonal block J in float64 shared memory (packed lower
-// triangle); zero its strict upper part.  A non-positive pivot sets
-// CR_ESINGULAR and is replaced by 1 so the factorisation runs to the end.
+// Factor the diagonal block J in shared memory (packed lower triangle, in
+// the factor precision: float64 is a narrow pipe on this GPU and the
+// float64 refinement corrects the float32 factor anyway); zero its strict
+// upper part.  A non-positive pivot sets CR_ESINGULAR and is replaced by 1
+// so the factorisation runs to the end.
 template <typename R>
 __global__ void __launch_bounds__(256) potrf_kernel(cpx<R>* __restrict__ L, int P, int J,
                                                     int* __restrict__ status) {
-    __shared__ cpx<double> a[NTRI];
-    __shared__ double piv;
+    __shared__ cpx<R> a[NTRI];
+    __shared__ R piv;
     __shared__ int bad;
     const int base = J * NB, n = min(NB, P - base), t = threadIdx.x;
     if (t == 0) bad = 0;
     for (int e = t; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
-        if (j <= i) a[tri(i, j)] = ccast<double>(L[(size_t)(base + i) * P + base + j]);
+        if (j <= i) a[tri(i, j)] = L[(size_t)(base + i) * P + base + j];
     }
     for (int j = 0; j < n; ++j) {
         __syncthreads();
         if (t == 0) {
-            double d = a[tri(j, j)].x;
-            if (!(d > 0.0)) {
+            R d = a[tri(j, j)].x;
+            if (!(d > R(0))) {
                 bad = 1;
-                d = 1.0;
+                d = R(1);
             }
-            piv = sqrt(d);
-            a[tri(j, j)] = {piv, 0.0};
+            piv = m_sqrt(d);
+            a[tri(j, j)] = {piv, R(0)};
         }
         __syncthreads();
-        const double ip = 1.0 / piv;
+        const R ip = R(1) / piv;
         for (int i = j + 1 + t; i < n; i += blockDim.x) a[tri(i, j)] = ip * a[tri(i, j)];
         __syncthreads();
         const int m = n - j - 1;
@@ -79,8 +82,7 @@ __global__ void __launch_bounds__(256) potrf_kernel(cpx<R>* __restrict__ L, int 
     __syncthreads();
     for (int e = t; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
-        L[(size_t)(base + i) * P + base + j] =
-            j <= i ? ccast<R>(a[tri(i, j)]) : cpx<R>{R(0), R(0)};
+        L[(size_t)(base + i) * P + base + j] = j <= i ? a[tri(i, j)] : cpx<R>{R(0), R(0)};
     }
     if (t == 0 && bad) set_status(status, CR_ESINGULAR);
 }
@@ -168,87 +170,109 @@ __global__ void __launch_bounds__(256) syrk_kernel(cpx<R>* __restrict__ L, int P
         }
 }
 
-// Block column J of L y = r: every CTA solves y_J = L_JJ^{-1} r_J (warp 0),
-// CTA 0 stores it; rows below get r_i -= L_iJ y_J (one warp per row).  r is
-// scratch (overwritten below block J), y the result.
+// Block column J of L y = r: every CTA stages L_JJ in shared memory and
+// solves y_J = L_JJ^{-1} r_J (warp 0), CTA 0 stores it; rows below get
+// r_i -= L_iJ y_J (one warp per row).  r is scratch (overwritten below
+// block J), y the result.
 template <typename R>
 __global__ void __launch_bounds__(256) trsv_fwd_kernel(const cpx<R>* __restrict__ L, int P, int J,
                                                        double* __restrict__ r_,
                                                        double* __restrict__ y_,
                                                        const double* __restrict__ skip) {
     if (*skip != 0.0) return;
-    __shared__ cpx<double> ys[NB];
+    __shared__ cpx<R> d[NTRI];
+    __shared__ cpx<R> ys[NB];
     cpx<double>* r = (cpx<double>*)r_;
     cpx<double>* y = (cpx<double>*)y_;
     const int base = J * NB, n = min(NB, P - base), t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    for (int e = t; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        if (j <= i) d[tri(i, j)] = L[(size_t)(base + i) * P + base + j];
+    }
+    __syncthreads();
     if (warp == 0) {
-        const cpx<double> z = {0.0, 0.0};
-        cpx<double> v0 = lane < n ? r[base + lane] : z, v1 = lane + 32 < n ? r[base + lane + 32] : z;
+        const cpx<R> z = {R(0), R(0)};
+        cpx<R> v0 = lane < n ? ccast<R>(r[base + lane]) : z;
+        cpx<R> v1 = lane + 32 < n ? ccast<R>(r[base + lane + 32]) : z;
         for (int c = 0; c < n; ++c) {
-            cpx<double> yc = shfl(c < 32 ? v0 : v1, c & 31);
-            yc = (1.0 / (double)L[(size_t)(base + c) * P + base + c].x) * yc;
+            cpx<R> yc = shfl(c < 32 ? v0 : v1, c & 31);
+            yc = (R(1) / d[tri(c, c)].x) * yc;
             if (lane == (c & 31)) {
                 if (c < 32) v0 = yc;
                 else v1 = yc;
             }
-            if (lane > c && lane < n)
-                v0 = v0 - ccast<double>(L[(size_t)(base + lane) * P + base + c]) * yc;
-            if (lane + 32 > c && lane + 32 < n)
-                v1 = v1 - ccast<double>(L[(size_t)(base + lane + 32) * P + base + c]) * yc;
+            if (lane > c && lane < n) v0 = v0 - d[tri(lane, c)] * yc;
+            if (lane + 32 > c && lane + 32 < n) v1 = v1 - d[tri(lane + 32, c)] * yc;
         }
         if (lane < n) ys[lane] = v0;
         if (lane + 32 < n) ys[lane + 32] = v1;
     }
     __syncthreads();
     if (blockIdx.x == 0)
-        for (int e = t; e < n; e += blockDim.x) y[base + e] = ys[e];
+        for (int e = t; e < n; e += blockDim.x) y[base + e] = ccast<double>(ys[e]);
     for (int row = base + n + blockIdx.x * 8 + warp; row < P; row += gridDim.x * 8) {
         const cpx<R>* Lr = L + (size_t)row * P + base;
-        cpx<double> s = ccast<double>(Lr[lane]) * ys[lane];
-        s = s + ccast<double>(Lr[lane + 32]) * ys[lane + 32];
+        cpx<R> s = Lr[lane] * ys[lane];
+        s = s + Lr[lane + 32] * ys[lane + 32];
         s = warp_sum(s);
-        if (lane == 0) r[row] = r[row] - s;
+        if (lane == 0) r[row] = r[row] - ccast<double>(s);
     }
 }
 
-// Block column J of L^dag x = y (J descending): every CTA solves
-// x_J = L_JJ^{-dag} y_J (warp 0), CTA 0 stores it; rows above get
-// y_i -= sum_c conj(L_{base + c, i}) x_c (one thread per row, coalesced).
+// Block column J of L^dag x = y (J descending): every CTA stages L_JJ in
+// shared memory and solves x_J = L_JJ^{-dag} y_J (warp 0), CTA 0 stores it;
+// the 32 rows i above the block that a CTA owns get
+// y_i -= sum_c conj(L_{base + c, i}) x_c (lanes along i, warps along c).
 template <typename R>
 __global__ void __launch_bounds__(256) trsv_bwd_kernel(const cpx<R>* __restrict__ L, int P, int J,
                                                        double* __restrict__ y_,
                                                        double* __restrict__ x_,
                                                        const double* __restrict__ skip) {
     if (*skip != 0.0) return;
-    __shared__ cpx<double> xs[NB];
+    __shared__ cpx<R> d[NTRI];
+    __shared__ cpx<R> xs[NB];
     cpx<double>* y = (cpx<double>*)y_;
     cpx<double>* x = (cpx<double>*)x_;
     const int base = J * NB, n = min(NB, P - base), t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    for (int e = t; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        if (j <= i) d[tri(i, j)] = L[(size_t)(base + i) * P + base + j];
+    }
+    __syncthreads();
     if (warp == 0) {
-        const cpx<double> z = {0.0, 0.0};
-        cpx<double> v0 = lane < n ? y[base + lane] : z, v1 = lane + 32 < n ? y[base + lane + 32] : z;
+        const cpx<R> z = {R(0), R(0)};
+        cpx<R> v0 = lane < n ? ccast<R>(y[base + lane]) : z;
+        cpx<R> v1 = lane + 32 < n ? ccast<R>(y[base + lane + 32]) : z;
         for (int c = n - 1; c >= 0; --c) {
-            const cpx<R>* Lc = L + (size_t)(base + c) * P + base;
-            cpx<double> xc = shfl(c < 32 ? v0 : v1, c & 31);
-            xc = (1.0 / (double)Lc[c].x) * xc;
+            cpx<R> xc = shfl(c < 32 ? v0 : v1, c & 31);
+            xc = (R(1) / d[tri(c, c)].x) * xc;
             if (lane == (c & 31)) {
                 if (c < 32) v0 = xc;
                 else v1 = xc;
             }
-            if (lane < c) v0 = v0 - conj(ccast<double>(Lc[lane])) * xc;
-            if (lane + 32 < c) v1 = v1 - conj(ccast<double>(Lc[lane + 32])) * xc;
+            if (lane < c) v0 = v0 - conj(d[tri(c, lane)]) * xc;
+            if (lane + 32 < c) v1 = v1 - conj(d[tri(c, lane + 32)]) * xc;
         }
         if (lane < n) xs[lane] = v0;
         if (lane + 32 < n) xs[lane + 32] = v1;
     }
     __syncthreads();
     if (blockIdx.x == 0)
-        for (int e = t; e < n; e += blockDim.x) x[base + e] = xs[e];
-    for (int i = blockIdx.x * blockDim.x + t; i < base; i += gridDim.x * blockDim.x) {
-        cpx<double> s = {0.0, 0.0};
-        for (int c = 0; c < n; ++c)
-            s = s + conj(ccast<double>(L[(size_t)(base + c) * P + i])) * xs[c];
-        y[i] = y[i] - s;
+        for (int e = t; e < n; e += blockDim.x) x[base + e] = ccast<double>(xs[e]);
+    // rows i in [32 blockIdx.x, +32): warp w sums the columns c in [8 w, 8 w + 8)
+    // (coalesced along i), then warp 0 adds the eight partial sums
+    __shared__ cpx<R> part[8][32];
+    const int i = blockIdx.x * 32 + lane;
+    cpx<R> s = {R(0), R(0)};
+    if (i < base)
+        for (int c = 8 * warp; c < 8 * warp + 8 && c < n; ++c)
+            s = s + conj(L[(size_t)(base + c) * P + i]) * xs[c];
+    part[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && i < base) {
+        cpx<R> tot = part[0][lane];
+        for (int w = 1; w < 8; ++w) tot = tot + part[w][lane];
+        y[i] = y[i] - ccast<double>(tot);
     }
 }
 
@@ -371,14 +395,14 @@ cr_status refine_t(cr_ctx* c, const double* F, int maxit) {
     for (int it = 0; it < maxit; ++it) {
         for (int J = 0; J < nb; ++J) {
             const int rows = P - (J + 1) * NB;
-            const int g = rows > 0 ? min((rows + 7) / 8, 2 * c->n_sm) : 1;
-            CR_LAUNCH(c, CR_KERNEL_CHOL,
+            const int g = rows > 0 ? (rows + 31) / 32 : 1;
+            CR_LAUNCH(c, CR_KERNEL_TRSV,
                       trsv_fwd_kernel<R><<<g, 256, 0, c->stream>>>(L, P, J, r, y, done));
         }
         for (int J = nb - 1; J >= 0; --J) {
             const int rows = J * NB;
-            const int g = rows > 0 ? min((rows + 255) / 256, 2 * c->n_sm) : 1;
-            CR_LAUNCH(c, CR_KERNEL_CHOL,
+            const int g = rows > 0 ? (rows + 31) / 32 : 1;
+            CR_LAUNCH(c, CR_KERNEL_TRSV,
                       trsv_bwd_kernel<R><<<g, 256, 0, c->stream>>>(L, P, J, y, d, done));
         }
         CR_LAUNCH(c, CR_K_OTHER, refine_resid_kernel<<<RES_GRID, 256, 0, c->stream>>>(
