@@ -9,7 +9,7 @@ then beta_n = <R> and mu_n with its Krylov columns.  Inputs are synthetic
 L2 is flushed between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload chain64|batch|square10]
+                  [--workload chain64|batch|square10|square16]
 
 --workload batch times the momentum scan instead: all 15 irreducible momenta
 of an 8 x 8 square lattice (q = 0 has a vanishing probe and is skipped) plus
@@ -22,6 +22,12 @@ alpha = 1 (P = 10,200), 32768 walkers, q = (pi, pi); S built on the tensor
 cores (three-term bf16 splits), blocked Cholesky in float32 refined in
 float64; it also reports |S_mixed - S_fp64|_F / |S_fp64|_F on a walker
 sample, for the default splits and for the cheaper two-term (bf16x3) form.
+
+--workload square16 times the largest lattice: 16 x 16, alpha = 1 (P =
+66,048), 65536 walkers, q = (pi, 0), matrix-free CG (float32 kernels: the
+tensor-core kernels cover M <= 256 only while their operands fit in shared
+memory), plus the Krylov step over 300 states (Gram estimators of 300
+sampled columns and the float64 generalized eigenproblem).
 
 Prints one JSON line.  Under torchrun every rank runs an independent
 sequence (a different seed): weak scaling with no data-path collective.
@@ -62,7 +68,12 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying CUDA graphs")
     ap.add_argument("--cpu-walkers", type=int, default=2048)
-    ap.add_argument("--workload", default="chain64", choices=["chain64", "batch", "square10"])
+    ap.add_argument("--chunks", type=int, default=None,
+                    help="walker chunks of the split-K reductions (default: the context's)")
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="chain64: skip the plain float32 path (tuning runs)")
+    ap.add_argument("--workload", default="chain64",
+                    choices=["chain64", "batch", "square10", "square16"])
     ap.add_argument("--s-error-walkers", type=int, default=2048,
                     help="square10: walkers of the tensor-core S vs float64 S comparison")
     return ap.parse_args()
@@ -183,13 +194,13 @@ def reduce_bytes(wl):
     return B * (8 * M + N + 8) + 16 * P
 
 
-def measure(args, prec_name, ws, rank, local):
-    """Time K moments of one precision path; returns (result dict, seq, ctx)."""
+def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
+    """Time K moments of one precision path; returns (result dict, config, workload)."""
     import torch
 
     from paper_2103_08804_gb300 import api, driver, synth
 
-    wl = synth.WORKLOADS[WORKLOAD]
+    wl = synth.WORKLOADS[wl_name]
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
     K, W = args.steps, args.warmup
     n_moments = 1 + W + 2 * K
@@ -198,6 +209,8 @@ def measure(args, prec_name, ws, rank, local):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = api.Context(wl.Lx, wl.Ly, wl.M, wl.walkers, prec=prec, stream=stream)
+    if args.chunks:
+        ctx.set_chunks(min(args.chunks, ctx.max_chunks()))
     psi = synth.rbm_params(seed, wl.N, wl.M, wl.sigma)
     cfg = make_config(wl, E0, a, args, n_moments, seed)
     seq = driver.Sequence(ctx, cfg, psi, synth.sz0_spins(seed + 2, wl.walkers, wl.N),
@@ -326,7 +339,7 @@ def run_ours(args):
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
     mixed, cfg, wl = measure(args, "mixed", ws, rank, local)
-    plain, _, _ = measure(args, "fp32", ws, rank, local)
+    plain = mixed if args.only_mixed else measure(args, "fp32", ws, rank, local)[0]
     merr = moment_error(args) if (rank == 0 and not args.no_accuracy) else None
     out = {
         "metric": "Chebyshev moments/hour",
@@ -349,7 +362,7 @@ def run_ours(args):
                    "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol, "jacobi": args.jacobi,
                    "l2": "256 MiB buffer written between timed steps",
                    "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
-                   "parallelism": f"replicas x{ws}"},
+                   "chunks": args.chunks, "parallelism": f"replicas x{ws}"},
         "mc_samples_per_s": mixed["mc_samples_per_s"],
         "mc_samples_unit": "walker-sweeps/s (one sweep = N exchange proposals)",
         "gpu_launches": mixed["gpu_launches"],
@@ -522,6 +535,65 @@ def roofline_reduce(ctx, seq, wl, clocks, n_eager=3):
     roof.update({"frac": (achieved / peak) if achieved else None, "traffic": None,
                  "launches_timed": len(ktimes), "avg_launch_ms": k_ms})
     return roof
+
+
+def run_square16(args):
+    """Matrix-free CG on the 16 x 16 lattice, plus the 300-state Krylov step."""
+    import torch
+
+    from paper_2103_08804_gb300 import api
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    res, cfg, wl = measure(args, "fp32", ws, rank, local, wl_name="square16")
+    # Krylov over Nm = 300 sampled columns B_n, (H' t_n)/psi of all 65536
+    # reference samples: timing of the Gram estimators and the eigenproblem
+    Nm, Bref = 300, wl.walkers
+    ctx = api.Context(wl.Lx, wl.Ly, wl.M, 64, prec=api.FP32)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    Bm = torch.randn(Nm, Bref, dtype=torch.complex64, device="cuda", generator=g)
+    HBm = torch.randn(Nm, Bref, dtype=torch.complex64, device="cuda", generator=g)
+    G = torch.empty(Nm, Nm, dtype=torch.complex128, device="cuda")
+    H = torch.empty_like(G)
+    mu = torch.zeros(2 * Nm, dtype=torch.complex128, device="cuda")
+    poles = torch.zeros(Nm, dtype=torch.float64, device="cuda")
+    wts = torch.zeros(Nm, dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    ctx.cheb_gram(Bm, HBm, G, H)
+    ev[1].record()
+    ctx.cheb_krylov(G, H, 1e-10, 2 * Nm, mu, poles, wts)
+    ev[2].record()
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    out = {
+        "metric": "Chebyshev moments/hour", "value": res["value"], "unit": "moments/hour",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 products, f64 sums and CG",
+        "data": "synthetic (random complex RBM, sigma=0.01; seeded S^z=0 walkers)",
+        "config": {"workload": "square16: periodic 16x16 Heisenberg lattice, RBM alpha=1 (M=256, "
+                               "P=66048), 65536 walkers, q=(pi,0), matrix-free CG shifted solve",
+                   "iters_per_moment": cfg.n_iter, "cg_maxit": args.cg_maxit,
+                   "cg_tol": args.cg_tol, "l2": "256 MiB buffer written between timed steps",
+                   "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
+                   "parallelism": f"replicas x{ws}"},
+        "mc_samples_per_s": res["mc_samples_per_s"], "gpu_launches": res["gpu_launches"],
+        "cg_iters_mean": res["cg_iters_mean"], "clocks": res["clocks"], "e2e": res["e2e"],
+        "roofline": res["roofline"],
+        "krylov_300": {"gram_ms": ev[0].elapsed_time(ev[1]),
+                       "eigen_ms": ev[1].elapsed_time(ev[2]),
+                       "note": "cheb_gram over 300 columns x 65536 samples, then cheb_krylov "
+                               "(pseudo-inverse, generalized eigenproblem, 600 corrected "
+                               "moments); once per sequence"},
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def run_explicit(args):
@@ -800,5 +872,7 @@ if __name__ == "__main__":
         run_batch(a)
     elif a.workload == "square10":
         run_explicit(a)
+    elif a.workload == "square16":
+        run_square16(a)
     else:
         run_ours(a)

@@ -22,6 +22,11 @@ cr_status cr_fail(cr_ctx* c, cr_status s, const char* fmt, ...) {
 
 bool cr_kt_begin(cr_ctx* c, int kid) {
     if (kid < 0 || c->kt.kid != kid || c->kt.count >= c->kt.cap) return false;
+    // launches being captured into a graph are not timed: an event record
+    // would only become a graph node, never a timestamp of this launch
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return false;
     cudaEventRecord(c->kt.ev[2 * c->kt.count], c->stream);
     return true;
 }

@@ -31,16 +31,6 @@ CR_D void split3(float x, __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* 
     *lo = __float2bfloat16_rn(r2);
 }
 
-// (hi, lo) += x with hi + lo kept to about twice float32 precision: Knuth's
-// TwoSum gives the rounding error of hi + x exactly, which lo collects.
-CR_D void two_sum_add(float& hi, float& lo, float x) {
-    const float s = __fadd_rn(hi, x);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-    hi = s;
-    lo = __fadd_rn(lo, e);
-}
-
 CR_D uint4 pack8(const __nv_bfloat16* v) {
     uint4 r;
     uint32_t* w = reinterpret_cast<uint32_t*>(&r);
@@ -420,30 +410,28 @@ __global__ void __launch_bounds__(RED_THREADS, 1) oreduce_tc_kernel(
 // number of MMAs added into one accumulator (measured: relative ~1e-8 per
 // accumulation), so a 128 x 256 tile of G is accumulated over chunks of CH
 // walkers in one TMEM half while the other half, holding the previous chunk,
-// is added into a compensated float32 accumulator (hi + lo pairs, TwoSum) in
-// shared memory: float64-like sums on the float32 pipe (the float64 pipe of
-// this GPU is far too narrow to keep up with the tensor cores).
+// is added into float32 accumulators in the registers of the drain warps
+// (the float64 pipe of this GPU is far too narrow to keep up with the tensor
+// cores), which leaves shared memory to a deep operand pipeline.
 //
 // xt_prep_kernel writes X^T as NPL bf16 planes, each an array of tiles
 // [row block of 128 G rows][walker chunk of KC] in the K-major no-swizzle
 // core-matrix layout, so one bulk copy moves one tile.
-// sgram_tc_kernel: persistent, 160 threads.  Warp 0 (one thread) copies
-// operand tiles through two stages and issues the MMAs of chunk c into TMEM
-// columns [256 (c % 2), +256); warps 1-4 (TMEM lanes 32 (w % 4) .. +31) wait
-// for the chunk, add it to the compensated tile of S (64 x 128 entries, formed
-// from adjacent lanes = rows 2k, 2k + 1), release the TMEM half, and at the
-// end of a tile write S and clear the accumulator.
+// sgram_tc_kernel: persistent, 288 threads.  Warp 0 (one thread) copies
+// operand tiles through NSTG stages (running ahead across tiles) and issues
+// the MMAs of chunk c into TMEM columns [256 (c % 2), +256); warps 1-8 wait
+// for the chunk, add it to their register tile of S (entries formed from
+// adjacent lanes = rows 2k, 2k + 1), release the TMEM half, and at the end
+// of a tile write S.
 template <int NPL>
 struct SGram {
     static constexpr int KC = NPL == 2 ? 32 : 16;    // walkers per operand tile
     static constexpr int TILE = 128 * KC * 2;         // bytes of one 128-row tile
-    static constexpr int NSTG = 2;                    // pipeline stages
     static constexpr int STAGE = NPL * 3 * TILE;      // A (1 row block) + B (2), NPL planes
+    static constexpr int NSTG = NPL == 2 ? 4 : 6;     // pipeline stages
     static constexpr int NPROD = NPL == 2 ? 3 : 6;
     static constexpr int CH = NPL == 2 ? 256 : 128;   // walkers per TMEM accumulation
-    static constexpr int ACC_LD = 129;                // padded row of the accumulator tile
-    static constexpr size_t ACC_BYTES = (size_t)64 * ACC_LD * 16;
-    static constexpr size_t SMEM = (size_t)NSTG * STAGE + ACC_BYTES + 128;
+    static constexpr size_t SMEM = (size_t)NSTG * STAGE + 256;
     // planes (A, B) of product pr: (hi, hi), (hi, mid), (mid, hi), (hi, lo),
     // (mid, mid), (lo, hi); NPL = 2 takes the first three (mid = lo there)
     static CR_HD int pa(int pr) {
@@ -455,7 +443,7 @@ struct SGram {
         return v[pr];
     }
 };
-constexpr int GR_THREADS = 160;
+constexpr int GR_THREADS = 288;
 
 template <int NPL>
 __global__ void xt_prep_kernel(const int8_t* __restrict__ spins, const cpx<float>* __restrict__ T,
@@ -509,18 +497,17 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
     using G = SGram<NPL>;
     constexpr int NSTG = G::NSTG, TILE = G::TILE, KPC = G::CH / G::KC;  // tiles per chunk
     extern __shared__ __align__(1024) unsigned char sm[];
-    float4* acc = (float4*)(sm + NSTG * G::STAGE);  // [64][ACC_LD] (Re hi, Re lo, Im hi, Im lo)
-    uint64_t* full = (uint64_t*)(sm + NSTG * G::STAGE + G::ACC_BYTES);
+    uint64_t* full = (uint64_t*)(sm + NSTG * G::STAGE);
     uint64_t* empty = full + NSTG;      // [NSTG] MMAs reading a stage done
     uint64_t* cdone = full + 2 * NSTG;  // [2] MMAs of a chunk done (per TMEM half)
-    uint64_t* drained = cdone + 2;      // [2] TMEM half read by the 128 drain threads
+    uint64_t* drained = cdone + 2;      // [2] TMEM half read by the 256 drain threads
     uint32_t* slot = (uint32_t*)(drained + 2);
     volatile int* abort = (volatile int*)(slot + 1);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     if (t == 0) {
         for (int i = 0; i < 2 * NSTG + 2; ++i) tc::mbar_init(&full[i], 1);
-        tc::mbar_init(&drained[0], 128);
-        tc::mbar_init(&drained[1], 128);
+        tc::mbar_init(&drained[0], 256);
+        tc::mbar_init(&drained[1], 256);
         tc::fence_mbar_init();
         *abort = 0;
     }
@@ -528,12 +515,12 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
         tc::tmem_alloc(slot, 512u);
         tc::tmem_relinquish();
     }
-    for (int e = t; e < 64 * G::ACC_LD; e += GR_THREADS) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *slot;
     const int nchunk = (nkc + KPC - 1) / KPC;
+    const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     // a bounded wait that also gives up once the other role has aborted
     auto wait = [&](uint64_t* bar, uint32_t par) {
         for (int i = 0; i < 64; ++i) {
@@ -546,71 +533,68 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
     if (warp == 0) {
         if (lane == 0) {
             // ---------------------------------------------- producer / MMA issuer
+            // One flat sequence of stages over all tiles of this CTA, so the
+            // copies run NSTG - 1 stages ahead across tile boundaries too.
             const uint32_t idesc = tc::make_idesc_bf16(128, 256);
-            uint32_t gs = 0, gc = 0;  // stages and chunks issued so far (all tiles)
+            const int total = nmine * nkc;
             uint32_t pend = 0, pend_par = 0;
-            int last_g = -1;          // last stage whose MMAs were committed
+            int last_g = -1;  // last stage whose MMAs were committed
             bool ok = true;
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            // copy the operands of stage g; its buffer was last read by the MMAs
+            // of stage g - NSTG
+            auto load = [&](int g) {
+                const uint32_t b = g % NSTG;
+                if (g >= NSTG && !wait(&empty[b], ((g - NSTG) / NSTG) & 1)) return false;
+                const int tile = blockIdx.x + (g / nkc) * gridDim.x, kc = g % nkc;
                 const int rt = tiles[tile].x, ct = tiles[tile].y;
-                const uint32_t gs0 = gs;
-                // copy the operands of stage gs0 + kc; its buffer was last read by
-                // the MMAs of stage gs0 + kc - NSTG (possibly of the previous tile)
-                auto load = [&](int kc) {
-                    const uint32_t g = gs0 + kc, b = g % NSTG;
-                    if (g >= NSTG && !wait(&empty[b], ((g - NSTG) / NSTG) & 1)) return false;
-                    pend |= 1u << b;
-                    pend_par = (pend_par & ~(1u << b)) | (((g / NSTG) & 1u) << b);
-                    unsigned char* st = sm + (size_t)b * G::STAGE;
-                    tc::mbar_expect_tx(&full[b], (uint32_t)G::STAGE);
-                    for (int pl = 0; pl < NPL; ++pl) {
-                        const unsigned char* src = Xt + (size_t)pl * plane_bytes;
-                        tc::bulk_g2s(st + pl * TILE, src + ((size_t)rt * nkc_max + kc) * TILE,
-                                     TILE, &full[b]);
-                        for (int q = 0; q < 2; ++q)
-                            tc::bulk_g2s(st + NPL * TILE + (pl * 2 + q) * TILE,
-                                         src + ((size_t)(2 * ct + q) * nkc_max + kc) * TILE, TILE,
-                                         &full[b]);
-                    }
-                    return true;
-                };
-                if (!load(0)) ok = false;
-                for (int kc = 0; kc < nkc && ok; ++kc) {
-                    const uint32_t g = gs0 + kc, b = g % NSTG;
-                    const int ck = kc / KPC, first = (kc % KPC) == 0;
-                    const uint32_t h = (gc + ck) & 1;
-                    // the TMEM half of chunk gc + ck was last used by chunk gc + ck - 2
-                    if (first && gc + ck >= 2 && !wait(&drained[h], ((gc + ck - 2) >> 1) & 1)) {
-                        ok = false;
-                        break;
-                    }
-                    if (!wait(&full[b], (g / NSTG) & 1)) {
-                        ok = false;
-                        break;
-                    }
-                    pend &= ~(1u << b);
-                    tc::fence_after_sync();
-                    const unsigned char* st = sm + (size_t)b * G::STAGE;
-                    const uint32_t a0 = tc::smem_u32(st), b0 = tc::smem_u32(st + NPL * TILE);
-#pragma unroll
-                    for (int ks = 0; ks < G::KC / 16; ++ks) {
-#pragma unroll
-                        for (int pr = 0; pr < G::NPROD; ++pr) {
-                            const uint64_t ad = tc::make_desc(
-                                a0 + G::pa(pr) * TILE + ks * 256, 128, 16 * G::KC);
-                            const uint64_t bd = tc::make_desc(
-                                b0 + G::pb(pr) * 2 * TILE + ks * 256, 128, 16 * G::KC);
-                            tc::mma_bf16(taddr + h * 256, ad, bd, idesc,
-                                         !(first && ks == 0 && pr == 0));
-                        }
-                    }
-                    tc::commit(&empty[b]);
-                    last_g = (int)g;
-                    if ((kc + 1) % KPC == 0 || kc + 1 == nkc) tc::commit(&cdone[h]);
-                    if (kc + 1 < nkc && !load(kc + 1)) ok = false;
+                pend |= 1u << b;
+                pend_par = (pend_par & ~(1u << b)) | (((uint32_t)(g / NSTG) & 1u) << b);
+                unsigned char* st = sm + (size_t)b * G::STAGE;
+                tc::mbar_expect_tx(&full[b], (uint32_t)G::STAGE);
+                for (int pl = 0; pl < NPL; ++pl) {
+                    const unsigned char* src = Xt + (size_t)pl * plane_bytes;
+                    tc::bulk_g2s(st + pl * TILE, src + ((size_t)rt * nkc_max + kc) * TILE, TILE,
+                                 &full[b]);
+                    for (int q = 0; q < 2; ++q)
+                        tc::bulk_g2s(st + NPL * TILE + (pl * 2 + q) * TILE,
+                                     src + ((size_t)(2 * ct + q) * nkc_max + kc) * TILE, TILE,
+                                     &full[b]);
                 }
-                gs += nkc;
-                gc += nchunk;
+                return true;
+            };
+            for (int g = 0; g < NSTG - 1 && g < total && ok; ++g) ok = load(g);
+            for (int g = 0; g < total && ok; ++g) {
+                const int kc = g % nkc, b = g % NSTG;
+                const int gc = (g / nkc) * nchunk + kc / KPC, first = (kc % KPC) == 0;
+                const uint32_t h = gc & 1;
+                // the TMEM half of chunk gc was last used by chunk gc - 2
+                if (first && gc >= 2 && !wait(&drained[h], ((gc - 2) >> 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                if (!wait(&full[b], (g / NSTG) & 1)) {
+                    ok = false;
+                    break;
+                }
+                pend &= ~(1u << b);
+                tc::fence_after_sync();
+                const unsigned char* st = sm + (size_t)b * G::STAGE;
+                const uint32_t a0 = tc::smem_u32(st), b0 = tc::smem_u32(st + NPL * TILE);
+#pragma unroll
+                for (int ks = 0; ks < G::KC / 16; ++ks) {
+#pragma unroll
+                    for (int pr = 0; pr < G::NPROD; ++pr) {
+                        const uint64_t ad =
+                            tc::make_desc(a0 + G::pa(pr) * TILE + ks * 256, 128, 16 * G::KC);
+                        const uint64_t bd =
+                            tc::make_desc(b0 + G::pb(pr) * 2 * TILE + ks * 256, 128, 16 * G::KC);
+                        tc::mma_bf16(taddr + h * 256, ad, bd, idesc, !(first && ks == 0 && pr == 0));
+                    }
+                }
+                tc::commit(&empty[b]);
+                last_g = g;
+                if ((kc + 1) % KPC == 0 || kc + 1 == nkc) tc::commit(&cdone[h]);
+                if (g + NSTG - 1 < total && !load(g + NSTG - 1)) ok = false;
             }
             if (!ok) {
                 *abort = 1;
@@ -624,17 +608,28 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
         }
         __syncwarp();
     } else {
-        // ---------------------------------------------------- drain (warps 1-4)
-        const int row = 32 * (warp & 3) + lane, odd = lane & 1, kl = row >> 1;
+        // ------------------------------------------------ drain (warps 1-8)
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (G rows) and columns
+        // [128 c2, +128) of the chunk's half, c2 = (w - 1) / 4; each lane keeps
+        // its 32 entries of S in float32 registers (chunk sums added with
+        // round-to-nearest: about sqrt(chunks) 2^-24 on top of each chunk's
+        // own error).
+        const int lb = warp & 3, c2 = (warp - 1) >> 2, odd = lane & 1;
+        const int row = 32 * lb + lane;
         const cpx<double>* redO = (const cpx<double>*)redO_;
         cpx<double>* S = (cpx<double>*)S_;
         const double inv = 1.0 / B;
-        const int d = t - 32;  // 0 .. 127
-        uint32_t gc = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        for (int ti = 0; ti < nmine && ok; ++ti) {
+            const int tile = blockIdx.x + ti * gridDim.x;
             const int rt = tiles[tile].x, ct = tiles[tile].y;
-            for (int ck = 0; ck < nchunk; ++ck, ++gc) {
+            float acc[8][4][2];  // [16-column chunk][entry][Re, Im]
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[ch][q][0] = acc[ch][q][1] = 0.f;
+            for (int ck = 0; ck < nchunk; ++ck) {
+                const int gc = ti * nchunk + ck;
                 const uint32_t h = gc & 1;
                 // warp-uniform outcome: tcgen05.ld below is a warp-wide instruction
                 if (!__all_sync(0xffffffffu, wait(&cdone[h], (gc >> 1) & 1))) {
@@ -642,10 +637,10 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
                     break;
                 }
                 tc::fence_after_sync();
-                float4* arow = acc + (size_t)kl * G::ACC_LD + 4 * odd;
-                for (int ch = 0; ch < 16; ++ch) {
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
                     float v[16], p[16];
-                    tc::tmem_ld16(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + h * 256 + ch * 16,
+                    tc::tmem_ld16(taddr + ((uint32_t)(32 * lb) << 16) + h * 256 + 128 * c2 + 16 * ch,
                                   v);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) p[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
@@ -656,9 +651,8 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
                         const float e1 = odd ? p[9 + 2 * q] : v[2 * q + 1];
                         const float o0 = odd ? v[8 + 2 * q] : p[2 * q];
                         const float o1 = odd ? v[9 + 2 * q] : p[2 * q + 1];
-                        float4& a = arow[8 * ch + q];
-                        two_sum_add(a.x, a.y, __fadd_rn(e0, o1));
-                        two_sum_add(a.z, a.w, __fsub_rn(e1, o0));
+                        acc[ch][q][0] = __fadd_rn(acc[ch][q][0], __fadd_rn(e0, o1));
+                        acc[ch][q][1] = __fadd_rn(acc[ch][q][1], __fsub_rn(e1, o0));
                     }
                 }
                 tc::fence_before_sync();
@@ -667,22 +661,25 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
                              : "memory");
             }
             if (!ok) break;
-            // tile done: S = acc / B - conj(Obar_k) Obar_l (+ shift), then clear
-            asm volatile("bar.sync 1, 128;\n" ::: "memory");
-            for (int e = d; e < 64 * 128; e += 128) {
-                const int i = e >> 7, j = e & 127, k = 64 * rt + i, l = 128 * ct + j;
-                float4& a = acc[(size_t)i * G::ACC_LD + j];
-                if (k < P && l < P) {
-                    const cpx<double> g = {(double)a.x + (double)a.y, (double)a.z + (double)a.w};
-                    cpx<double> val = inv * g - conj(inv * redO[k]) * (inv * redO[l]);
-                    if (k == l) val.x += shift;
-                    S[(size_t)k * P + l] = val;
-                }
-                a = make_float4(0.f, 0.f, 0.f, 0.f);
+            // tile done: S = acc / B - conj(Obar_k) Obar_l (+ shift)
+            const int k = 64 * rt + (row >> 1);
+            if (k < P) {
+                const cpx<double> obk = conj(inv * redO[k]);
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int l = 128 * ct + 64 * c2 + 8 * ch + 4 * odd + q;
+                        if (l < P) {
+                            const cpx<double> g = {(double)acc[ch][q][0], (double)acc[ch][q][1]};
+                            cpx<double> val = inv * g - obk * (inv * redO[l]);
+                            if (k == l) val.x += shift;
+                            S[(size_t)k * P + l] = val;
+                        }
+                    }
             }
-            asm volatile("bar.sync 1, 128;\n" ::: "memory");
         }
-        if (!ok && d == 0) set_status(status, CR_ETIMEOUT);
+        if (!ok && t == 32) set_status(status, CR_ETIMEOUT);
     }
     tc::fence_before_sync();
     __syncthreads();
