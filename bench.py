@@ -209,6 +209,14 @@ BATCH_CYCLE_NOTE = ("every timed step is moment 3 (the n >= 3 target) of every s
                     "untimed restart (|psi|^2 sampled, moments 1-2 fitted)")
 
 
+# DRAM bytes (read + write) of one launch of the roofline kernel, from an
+# ncu capture of the current kernel on the same workload.
+MEASURED_TRAFFIC = {
+    ("mixed", "chain64"): (18002176, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                     "oreduce_tc_kernel launch on chain64 (18.00 MB + 0)"),
+}
+
+
 def reduce_flops(wl):
     """Algorithmic flops of one launch of the O-reduction over all walkers:
     per (walker, i, j) one real x complex FMA for O_W (4 flops), per (walker, j)
@@ -314,7 +322,10 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "work_per_launch": reduce_bytes(wl),
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
-    roof.update({"frac": (achieved / peak) if achieved else None, "traffic": None,
+    traffic = MEASURED_TRAFFIC.get((prec_name, wl_name))
+    roof.update({"frac": (achieved / peak) if achieved else None,
+                 "traffic": traffic[0] if traffic else None,
+                 "traffic_source": traffic[1] if traffic else None,
                  "launches_timed": len(ktimes), "avg_launch_ms": k_ms})
     sweeps_per_moment = cfg.n_therm + cfg.n_iter * cfg.sweeps_per_iter + cfg.sweeps_per_iter
     res = {"value": ws * 3600.0 * 1000.0 / ms, "ms_per_step": ms,
