@@ -29,6 +29,9 @@ equations in the paper's order; library primitives (matrix products,
   chebyshev -- the Chebyshev recursion driver and the moments (Secs. II-III).
   krylov    -- moment correction and the Krylov (generalised
                eigenproblem) projection (Secs. IV-V).
+  spectrum  -- the spectral function on a frequency grid: Chebyshev sum
+               with Jackson damping (Secs. II, V) and the continued
+               fraction of the Krylov projection (Sec. IV).
 """
 
-from . import lattice, philox, rbm, sampler, target, sr, exact, chebyshev, krylov  # noqa: F401
+from . import lattice, philox, rbm, sampler, target, sr, exact, chebyshev, krylov, spectrum  # noqa: F401
