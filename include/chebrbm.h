@@ -298,6 +298,28 @@ cr_status logpsi_backward_noalloc(int N, int M, cr_prec prec, const int8_t* spin
 cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, const void* tanh_theta,
                   const void* R, int B, const cr_sr_opts* opts, double* stats_out);
 
+/* Sec. II, Eq. (Aw), with the Jackson damping of Sec. V: the spectral
+   function on a frequency grid from the moments mu_n, n = 0 .. Nm - 1,
+     A(omega) = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n T_n(omega')]
+                / (a pi sqrt(1 - omega'^2)),   omega' = omega / a - W',
+   (the paper's prefactor 2 W'/W_* is 1/a), and 0 where |omega'| >= 1.
+   g_n = ((Nm - n + 1) cos(pi n/(Nm+1)) + sin(pi n/(Nm+1)) cot(pi/(Nm+1)))
+   / (Nm + 1) when jackson = 1, else 1.  mu: device complex128 [Nm]
+   (1 <= Nm <= 12800); omega: device float64 [n_omega] (excitation energies
+   E - E0); A_out: device complex128 [n_omega].  Float64 throughout. */
+cr_status cheb_spectrum(cr_ctx* ctx, const double* mu, int Nm, double a, double Wp,
+                        int jackson, const double* omega, int n_omega, double* A_out);
+
+/* Sec. IV: the spectral function of the Krylov projection, broadened by
+   eta, from its poles lambda_k (H' units) and weights w_k (cheb_krylov):
+     A(omega) = -Im sum_k w_k / (omega' + i eta/a - lambda_k) / (pi a),
+   the same function the continued fraction of the Lanczos tridiagonal form
+   evaluates.  poles, weights: device float64 [K]; omega, A_out: device
+   float64 [n_omega].  Needs a > 0, eta > 0. */
+cr_status cheb_lorentzian(cr_ctx* ctx, const double* poles, const double* weights, int K,
+                          double a, double Wp, double eta, const double* omega, int n_omega,
+                          double* A_out);
+
 /* Sec. III: the explicit S + shift I of sr_step's Cholesky path, built by
    the same kernels on samples of |psi|^2 (Obar from the same samples), copied
    to S_out: device complex128 [P][P], the full Hermitian matrix.  For

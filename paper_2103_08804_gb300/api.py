@@ -27,7 +27,8 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds", "rbm_logpsi", "mc_sweep",
            "cheb_local_target", "logderiv", "logpsi_backward", "sr_step", "cheb_moment",
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
-           "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix")
+           "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix",
+           "cheb_spectrum", "cheb_lorentzian")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
           "chol": 7, "trsv": 8}
 
@@ -96,6 +97,8 @@ def load(path=None):
     lib.cr_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i]
     lib.cr_set_chunks.argtypes = [vp, i]
     lib.sr_smatrix.argtypes = [vp, vp, vp, i, d, vp]
+    lib.cheb_spectrum.argtypes = [vp, vp, i, d, d, i, vp, i, vp]
+    lib.cheb_lorentzian.argtypes = [vp, vp, vp, i, d, d, d, vp, i, vp]
     lib.cr_max_chunks.argtypes = [vp]
     lib.logpsi_backward_noalloc.argtypes = [i, i, i, vp, vp, i, vp, vp, vp, ctypes.c_char_p, i]
     for f in SYMBOLS:
@@ -307,6 +310,30 @@ class Context:
         self._check(self.lib.sr_smatrix(self.h, _ptr(spins), _ptr(tanh_theta), B, float(shift),
                                         _ptr(S_out)), "sr_smatrix")
         return S_out
+
+    def cheb_spectrum(self, mu, a, Wp, omega, jackson=True):
+        """A(omega) of Eq. (Aw) (complex128 [len(omega)]) from the moments mu."""
+        for t, name in ((mu, "mu"), (omega, "omega")):
+            if not (t.is_cuda and t.is_contiguous()):
+                raise ValueError(f"{name}: need a contiguous CUDA tensor")
+        if mu.dtype != torch.complex128 or omega.dtype != torch.float64:
+            raise ValueError("mu: complex128, omega: float64")
+        out = torch.empty(omega.numel(), dtype=torch.complex128, device=omega.device)
+        self._check(self.lib.cheb_spectrum(self.h, _ptr(mu), mu.numel(), float(a), float(Wp),
+                                           1 if jackson else 0, _ptr(omega), omega.numel(),
+                                           _ptr(out)), "cheb_spectrum")
+        return out
+
+    def cheb_lorentzian(self, poles, weights, a, Wp, eta, omega):
+        """The eta-broadened spectral function of the Krylov projection."""
+        for t in (poles, weights, omega):
+            if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.float64):
+                raise ValueError("poles, weights, omega: contiguous CUDA float64")
+        out = torch.empty(omega.numel(), dtype=torch.float64, device=omega.device)
+        self._check(self.lib.cheb_lorentzian(self.h, _ptr(poles), _ptr(weights), poles.numel(),
+                                             float(a), float(Wp), float(eta), _ptr(omega),
+                                             omega.numel(), _ptr(out)), "cheb_lorentzian")
+        return out
 
     def cheb_moment(self, state, beta, q, spins, logpsi_ref, hprime=None, Bcol=None, HBcol=None,
                     mu_out=None):
