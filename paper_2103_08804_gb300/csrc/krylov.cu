@@ -67,176 +67,282 @@ extern "C" cr_status cheb_gram(cr_ctx* ctx, const void* Bmat, const void* HBmat,
 }
 
 // ------------------------------------------------------------- Jacobi
+//
+// Cyclic Jacobi on many CTAs.  Each sweep has m - 1 rounds (round-robin
+// pairing of the m indices: position 0 fixed, the others rotating); a round
+// applies its m/2 disjoint rotations at once, A' = J^T A J and V' = V J, out
+// of place (ping-pong buffers), one launch per round.  Every CTA computes
+// the rotation angles of the pairs its 32 x 32 output tile touches from the
+// round's input, so no launch waits on another.  Between sweeps the
+// off-diagonal norm is reduced (fixed order) and, once it is below
+// JAC_TOL times the diagonal, a device flag makes every later launch return
+// at once; `res` records which buffer holds the latest A and V.
+
+namespace {
+
+constexpr int JAC_MAX_SWEEPS = 30;
+constexpr double JAC_TOL = 1e-24;  // off^2 <= JAC_TOL diag^2 (relative 1e-12)
+constexpr int NORM_GRID = 128;
 
 // Element of the round-robin schedule: position 0 is fixed, the others
 // rotate by one place per round.
 __device__ __forceinline__ int rr_elem(int pos, int round, int m) {
     return pos == 0 ? 0 : ((pos - 1 + round) % (m - 1)) + 1;
 }
+// Position of index idx in round `round` (inverse of rr_elem).
+__device__ __forceinline__ int rr_pos(int idx, int round, int m) {
+    return idx == 0 ? 0 : ((idx - 1 - round) % (m - 1) + (m - 1)) % (m - 1) + 1;
+}
 
-// Diagonalise the symmetric m x m matrix A (row-major, in place; m even)
-// and accumulate the rotations into V (V = eigenvectors as columns).
-// cs: scratch [m] (cos, sin per pair).  Whole CTA participates.
-__device__ void jacobi_sym(double* A, double* V, int m, double* cs, int max_sweeps) {
-    __shared__ double red[32];
-    __shared__ int stop;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) V[e] = (e / m == e % m) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double off = 0.0, dia = 0.0;
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            double v = A[e] * A[e];
-            if (e / m == e % m) dia += v;
-            else off += v;
-        }
-        __syncthreads();
-        off = warp_sum(off);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-            red[0] = t;
-        }
-        __syncthreads();
-        off = red[0];
-        __syncthreads();
-        dia = warp_sum(dia);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dia;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-            stop = !(off > 1e-30 * t) ? 1 : 0;
-        }
-        __syncthreads();
-        if (stop) break;
-        for (int round = 0; round < m - 1; ++round) {
-            // rotation angles for the m/2 disjoint pairs of this round
-            for (int k = threadIdx.x; k < m / 2; k += blockDim.x) {
-                int p = rr_elem(k, round, m), q = rr_elem(m - 1 - k, round, m);
-                double apq = A[(size_t)p * m + q], c = 1.0, s = 0.0;
-                if (apq != 0.0) {
-                    double tau = (A[(size_t)q * m + q] - A[(size_t)p * m + p]) / (2.0 * apq);
-                    double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    s = t * c;
-                }
-                cs[2 * k] = c;
-                cs[2 * k + 1] = s;
+struct JacBufs {
+    double* A[2];
+    double* V[2];
+    int* res;   // index of the buffers holding the latest A, V
+    int* flag;  // converged
+};
+
+__global__ void jac_init_kernel(JacBufs J, int m) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx == 0) {
+        *J.res = 0;
+        *J.flag = 0;
+    }
+    if (idx < (size_t)m * m) J.V[0][idx] = (idx / m == idx % m) ? 1.0 : 0.0;
+}
+
+__global__ void __launch_bounds__(256) jac_round_kernel(JacBufs J, int m, int round, int in) {
+    if (*J.flag) return;
+    __shared__ double ang_c[64], ang_s[64];
+    __shared__ int partner[64], role[64];
+    const double* A = J.A[in];
+    const double* V = J.V[in];
+    double* Ao = J.A[in ^ 1];
+    double* Vo = J.V[in ^ 1];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, t = threadIdx.x;
+    if (t < 64) {
+        const int idx = (t < 32 ? i0 : j0) + (t & 31);
+        double c = 1.0, sn = 0.0;
+        int pt = idx, rl = 0;
+        if (idx < m) {
+            const int pos = rr_pos(idx, round, m);
+            const int k = pos < m / 2 ? pos : m - 1 - pos;
+            const int p = rr_elem(k, round, m), q = rr_elem(m - 1 - k, round, m);
+            const double apq = A[(size_t)p * m + q];
+            if (apq != 0.0) {
+                const double tau = (A[(size_t)q * m + q] - A[(size_t)p * m + p]) / (2.0 * apq);
+                const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                c = 1.0 / sqrt(1.0 + tt * tt);
+                sn = tt * c;
             }
-            __syncthreads();
-            // A <- A J (columns p, q) and V <- V J
-            for (int e = threadIdx.x; e < (m / 2) * m; e += blockDim.x) {
-                int k = e / m, r = e % m;
-                int p = rr_elem(k, round, m), q = rr_elem(m - 1 - k, round, m);
-                double c = cs[2 * k], s = cs[2 * k + 1];
-                double ap = A[(size_t)r * m + p], aq = A[(size_t)r * m + q];
-                A[(size_t)r * m + p] = c * ap - s * aq;
-                A[(size_t)r * m + q] = s * ap + c * aq;
-                double vp = V[(size_t)r * m + p], vq = V[(size_t)r * m + q];
-                V[(size_t)r * m + p] = c * vp - s * vq;
-                V[(size_t)r * m + q] = s * vp + c * vq;
-            }
-            __syncthreads();
-            // A <- J^T A (rows p, q)
-            for (int e = threadIdx.x; e < (m / 2) * m; e += blockDim.x) {
-                int k = e / m, r = e % m;
-                int p = rr_elem(k, round, m), q = rr_elem(m - 1 - k, round, m);
-                double c = cs[2 * k], s = cs[2 * k + 1];
-                double ap = A[(size_t)p * m + r], aq = A[(size_t)q * m + r];
-                A[(size_t)p * m + r] = c * ap - s * aq;
-                A[(size_t)q * m + r] = s * ap + c * aq;
-            }
-            __syncthreads();
+            pt = idx == p ? q : p;
+            rl = idx == p ? 0 : 1;
         }
+        ang_c[t] = c;
+        ang_s[t] = sn;
+        partner[t] = pt;
+        role[t] = rl;
     }
     __syncthreads();
+    for (int e = t; e < 1024; e += blockDim.x) {
+        const int li = e >> 5, lj = e & 31, i = i0 + li, j = j0 + lj;
+        if (i >= m || j >= m) continue;
+        const double ci = ang_c[li], si = ang_s[li], cj = ang_c[32 + lj], sj = ang_s[32 + lj];
+        const int ip = partner[li], jp = partner[32 + lj];
+        // column step (pair of j) on rows i and i', then the row step (pair of i)
+        const double sgj = role[32 + lj] ? sj : -sj, sgi = role[li] ? si : -si;
+        const double bij = cj * A[(size_t)i * m + j] + sgj * A[(size_t)i * m + jp];
+        const double bpj = cj * A[(size_t)ip * m + j] + sgj * A[(size_t)ip * m + jp];
+        Ao[(size_t)i * m + j] = ci * bij + sgi * bpj;
+        Vo[(size_t)i * m + j] = cj * V[(size_t)i * m + j] + sgj * V[(size_t)i * m + jp];
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && t == 0) *J.res = in ^ 1;
 }
 
-// Real symmetric embedding of a complex Hermitian n x n matrix.
-__device__ void embed(const cpx<double>* A, int n, double* E) {
-    const int m = 2 * n;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        int i = e / n, j = e % n;
-        cpx<double> a = A[e];
-        E[(size_t)i * m + j] = a.x;
-        E[(size_t)(i + n) * m + j + n] = a.x;
-        E[(size_t)(i + n) * m + j] = a.y;
-        E[(size_t)i * m + j + n] = -a.y;
+// Per-CTA shares of the squared off-diagonal and diagonal sums of A[res].
+__global__ void __launch_bounds__(256) jac_norm_kernel(JacBufs J, int m, double* __restrict__ part) {
+    if (*J.flag) return;
+    __shared__ double r1[8], r2[8];
+    const double* A = J.A[*J.res];
+    double off = 0.0, dia = 0.0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)m * m;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const double v = A[e] * A[e];
+        if (e / m == e % m) dia += v;
+        else off += v;
+    }
+    off = warp_sum(off);
+    dia = warp_sum(dia);
+    if ((threadIdx.x & 31) == 0) {
+        r1[threadIdx.x >> 5] = off;
+        r2[threadIdx.x >> 5] = dia;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            a += r1[w];
+            b += r2[w];
+        }
+        part[blockIdx.x] = a;
+        part[NORM_GRID + blockIdx.x] = b;
     }
 }
 
-// Workspace layout (doubles): E [m*m], V [m*m], X [m*m], Y [m*m], small vectors.
-__global__ void __launch_bounds__(1024) krylov_kernel(const double* __restrict__ G_,
-                                                      const double* __restrict__ H_, int n,
-                                                      double cutoff, int n_out, double* __restrict__ ws,
-                                                      double* __restrict__ mu_out,
-                                                      double* __restrict__ poles,
-                                                      double* __restrict__ weights,
-                                                      int32_t* __restrict__ rank_out) {
+__global__ void jac_flag_kernel(JacBufs J, const double* __restrict__ part) {
+    if (*J.flag) return;
+    double off = 0.0, dia = 0.0;
+    for (int b = 0; b < NORM_GRID; ++b) {
+        off += part[b];
+        dia += part[NORM_GRID + b];
+    }
+    if (!(off > JAC_TOL * dia)) *J.flag = 1;
+}
+
+// Diagonalise the symmetric m x m matrix in J.A[0] (m even); eigenvalues on
+// the diagonal of J.A[*res], eigenvectors in the columns of J.V[*res].
+void jacobi_launch(cr_ctx* c, JacBufs J, int m, double* part) {
+    const size_t mm = (size_t)m * m;
+    CR_LAUNCH(c, CR_K_OTHER, jac_init_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, c->stream>>>(J, m));
+    const dim3 g((m + 31) / 32, (m + 31) / 32);
+    int in = 0;
+    for (int sweep = 0; sweep < JAC_MAX_SWEEPS; ++sweep) {
+        CR_LAUNCH(c, CR_K_OTHER, jac_norm_kernel<<<NORM_GRID, 256, 0, c->stream>>>(J, m, part));
+        CR_LAUNCH(c, CR_K_OTHER, jac_flag_kernel<<<1, 1, 0, c->stream>>>(J, part));
+        for (int round = 0; round < m - 1; ++round) {
+            CR_LAUNCH(c, CR_K_OTHER, jac_round_kernel<<<g, 256, 0, c->stream>>>(J, m, round, in));
+            in ^= 1;
+        }
+    }
+}
+
+// Real symmetric embedding [[Ar, -Ai], [Ai, Ar]] of a complex Hermitian n x n
+// matrix (every eigenvalue twice, eigenvector pairs [ur; ui], [-ui; ur]).
+__global__ void kry_embed_kernel(const double* __restrict__ A_, int n, double* __restrict__ E) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    const int m = 2 * n, i = e / n, j = e % n;
+    const cpx<double> a = ((const cpx<double>*)A_)[e];
+    E[(size_t)i * m + j] = a.x;
+    E[(size_t)(i + n) * m + j + n] = a.x;
+    E[(size_t)(i + n) * m + j] = a.y;
+    E[(size_t)i * m + j + n] = -a.y;
+}
+
+// Eigenvalues of the embedded G, the kept index list (relative cutoff; an
+// odd count drops the smallest, the copy a cutoff split by rounding) and
+// the rank r (even).  One thread.
+__global__ void kry_keep_kernel(JacBufs J, int m, double cutoff, double* __restrict__ d,
+                                int* __restrict__ keep, int* __restrict__ rank) {
+    const double* E = J.A[*J.res];
+    double dm = 0.0;
+    for (int k = 0; k < m; ++k) {
+        d[k] = E[(size_t)k * m + k];
+        dm = d[k] > dm ? d[k] : dm;
+    }
+    int r = 0;
+    for (int k = 0; k < m; ++k)
+        if (d[k] > cutoff * dm) keep[r++] = k;
+    if (r & 1) {
+        int lo = 0;
+        for (int q = 1; q < r; ++q)
+            if (d[keep[q]] < d[keep[lo]]) lo = q;
+        for (int q = lo; q < r - 1; ++q) keep[q] = keep[q + 1];
+        --r;
+    }
+    *rank = r;
+}
+
+// Y[i][j] = sum_kept V[i][k] V[j][k] / d[k], i < m, j < n: the pseudo-inverse
+// of the embedded G, first n columns (G^+ = Y[0:n] + i Y[n:2n]).
+__global__ void kry_pinv_kernel(JacBufs J, int m, const double* __restrict__ d,
+                                const int* __restrict__ keep, const int* __restrict__ rank,
+                                double* __restrict__ Y) {
+    const int n = m / 2;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * n) return;
+    const double* V = J.V[*J.res];
+    const int i = e / n, j = e % n, r = *rank;
+    double s = 0.0;
+    for (int q = 0; q < r; ++q) {
+        const int k = keep[q];
+        s += V[(size_t)i * m + k] * V[(size_t)j * m + k] / d[k];
+    }
+    Y[e] = s;
+}
+
+// X[i][q] = V[i][keep q] / sqrt(d) for q < r, 0 for r <= q < m (padding).
+__global__ void kry_x_kernel(JacBufs J, int m, const double* __restrict__ d,
+                             const int* __restrict__ keep, const int* __restrict__ rank,
+                             double* __restrict__ X) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int i = e / m, q = e % m, r = *rank;
+    const double* V = J.V[*J.res];
+    X[e] = q < r ? V[(size_t)i * m + keep[q]] / sqrt(d[keep[q]]) : 0.0;
+}
+
+// C = A^T B or A B (m x m, row-major), one output per thread (float64).
+template <bool TRANS_A>
+__global__ void kry_gemm_kernel(const double* __restrict__ A, const double* __restrict__ B, int m,
+                                double* __restrict__ C) {
+    __shared__ double as[16][17], bs[16][17];
+    const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+    double s = 0.0;
+    for (int l0 = 0; l0 < m; l0 += 16) {
+        const int la = l0 + threadIdx.x, lb = l0 + threadIdx.y;
+        const int ia = blockIdx.y * 16 + threadIdx.y;
+        as[threadIdx.y][threadIdx.x] =
+            (ia < m && la < m) ? (TRANS_A ? A[(size_t)la * m + ia] : A[(size_t)ia * m + la]) : 0.0;
+        bs[threadIdx.y][threadIdx.x] = (lb < m && j < m) ? B[(size_t)lb * m + j] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) s += as[threadIdx.y][q] * bs[q][threadIdx.x];
+        __syncthreads();
+    }
+    if (i < m && j < m) C[(size_t)i * m + j] = s;
+}
+
+// out = (C + C^T) / 2 into the Jacobi input buffer; g0 = X^T [Re G e0; Im G e0].
+__global__ void kry_sym_kernel(const double* __restrict__ C, int m, double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int a = e / m, b = e % m;
+    out[e] = 0.5 * (C[e] + C[(size_t)b * m + a]);
+}
+
+__global__ void kry_g0_kernel(const double* __restrict__ G_, const double* __restrict__ X, int m,
+                              double* __restrict__ g0) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    const int n = m / 2;
+    const cpx<double>* G = (const cpx<double>*)G_;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) {
+        const cpx<double> gl = G[(size_t)l * n];
+        s += X[(size_t)l * m + q] * gl.x + X[(size_t)(l + n) * m + q] * gl.y;
+    }
+    g0[q] = s;
+}
+
+// Moment correction (one CTA): c_0 = e_0, c_1 = G^+ H c_0,
+// c_{k+1} = G^+ (2 H c_k - G c_{k-1}); mu'_k = (G c_k)_0.
+__global__ void __launch_bounds__(1024) kry_moments_kernel(const double* __restrict__ G_,
+                                                           const double* __restrict__ H_, int n,
+                                                           const double* __restrict__ Y, int n_out,
+                                                           double* __restrict__ vec,
+                                                           double* __restrict__ mu_out) {
     const cpx<double>* G = (const cpx<double>*)G_;
     const cpx<double>* H = (const cpx<double>*)H_;
-    const int m = 2 * n;
-    const size_t mm = (size_t)m * m;
-    double* E = ws;
-    double* V = ws + mm;
-    double* X = ws + 2 * mm;
-    double* Y = ws + 3 * mm;
-    double* d = ws + 4 * mm;       // [m] eigenvalues of the embedded G
-    double* cs = d + m;            // [m]
-    double* w = cs + m;            // [m]
-    cpx<double>* c0 = (cpx<double>*)(w + m);   // [n] x 4 complex vectors
+    cpx<double>* c0 = (cpx<double>*)vec;
     cpx<double>* c1 = c0 + n;
     cpx<double>* t1 = c1 + n;
     cpx<double>* t2 = t1 + n;
-    __shared__ int s_keep[1024];
-    __shared__ int s_rank;
-
-    // 1. G = U L U^dag through the embedding
-    embed(G, n, E);
-    __syncthreads();
-    jacobi_sym(E, V, m, cs, 60);
-    for (int k = threadIdx.x; k < m; k += blockDim.x) d[k] = E[(size_t)k * m + k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double dm = 0.0;
-        for (int k = 0; k < m; ++k) dm = d[k] > dm ? d[k] : dm;
-        int r = 0;
-        for (int k = 0; k < m; ++k)
-            if (d[k] > cutoff * dm) s_keep[r++] = k;
-        if (r & 1) {
-            // the embedding doubles every eigenvalue; a cutoff that splits a
-            // pair by rounding drops the smaller copy
-            int lo = 0;
-            for (int q = 1; q < r; ++q)
-                if (d[s_keep[q]] < d[s_keep[lo]]) lo = q;
-            for (int q = lo; q < r - 1; ++q) s_keep[q] = s_keep[q + 1];
-            --r;
-        }
-        s_rank = r;
-    }
-    __syncthreads();
-    const int r = s_rank;
-    // 2. pseudo-inverse G^+ in the embedding: Y = sum_kept v v^T / d
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e / m, j = e % m;
-        double s = 0.0;
-        for (int q = 0; q < r; ++q) {
-            int k = s_keep[q];
-            s += V[(size_t)i * m + k] * V[(size_t)j * m + k] / d[k];
-        }
-        Y[e] = s;
-    }
-    __syncthreads();
-    // 3. moment correction: c_0 = e_0, c_1 = G^+ H c_0, c_{k+1} = G^+ (2 H c_k - G c_{k-1});
-    //    mu'_k = (G c_k)_0.  G^+ = Y[0:n,0:n] + i Y[n:2n,0:n].
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         c0[i] = {i == 0 ? 1.0 : 0.0, 0.0};
         c1[i] = {0.0, 0.0};
     }
     __syncthreads();
     for (int k = 0; k < n_out; ++k) {
-        // mu'_k = sum_l G_0l c_k[l]
         if (threadIdx.x == 0) {
             cpx<double> s = {0.0, 0.0};
             for (int l = 0; l < n; ++l) s = s + G[l] * c0[l];
@@ -257,7 +363,7 @@ __global__ void __launch_bounds__(1024) krylov_kernel(const double* __restrict__
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             cpx<double> s = {0.0, 0.0};
             for (int l = 0; l < n; ++l) {
-                cpx<double> gp = {Y[(size_t)i * m + l], Y[(size_t)(i + n) * m + l]};
+                const cpx<double> gp = {Y[(size_t)i * n + l], Y[(size_t)(i + n) * n + l]};
                 s = s + gp * t1[l];
             }
             t2[i] = s;
@@ -269,73 +375,45 @@ __global__ void __launch_bounds__(1024) krylov_kernel(const double* __restrict__
         }
         __syncthreads();
     }
-    __syncthreads();
-    // 4. projected eigenproblem: Xh = Vk diag(d^-1/2) (m x r), Hx = Xh^T Hemb Xh
-    embed(H, n, E);
-    __syncthreads();
-    // X[i][q] = V[i][keep q] / sqrt(d)
-    for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
-        int i = e / r, q = e % r, k = s_keep[q];
-        X[(size_t)i * r + q] = V[(size_t)i * m + k] / sqrt(d[k]);
-    }
-    __syncthreads();
-    // Y = Hemb X  (m x r)
-    for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
-        int i = e / r, q = e % r;
-        double s = 0.0;
-        for (int l = 0; l < m; ++l) s += E[(size_t)i * m + l] * X[(size_t)l * r + q];
-        Y[e] = s;
-    }
-    __syncthreads();
-    // E = X^T Y (r x r), symmetrised
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-        int a = e / r, b = e % r;
-        double s = 0.0;
-        for (int l = 0; l < m; ++l) s += X[(size_t)l * r + a] * Y[(size_t)l * r + b];
-        V[e] = s;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-        int a = e / r, b = e % r;
-        E[e] = 0.5 * (V[e] + V[(size_t)b * r + a]);
-    }
-    __syncthreads();
-    // g0 = X^T (G e_0 embedded) = X^T [Re G[:,0]; Im G[:,0]]
-    for (int q = threadIdx.x; q < r; q += blockDim.x) {
-        double s = 0.0;
-        for (int l = 0; l < n; ++l) {
-            cpx<double> gl = G[(size_t)l * n];
-            s += X[(size_t)l * r + q] * gl.x + X[(size_t)(l + n) * r + q] * gl.y;
-        }
-        w[q] = s;
-    }
-    __syncthreads();
-    jacobi_sym(E, V, r, cs, 60);   // r is even: kept eigenvalues come in pairs
-    // eigenvalue k: E[k][k]; weight: (V[:,k] . g0)^2
+}
+
+// Poles and weights from the diagonalised projection (one CTA): eigenvalue
+// k = E[k][k] for k < r, weight (V[:, k] . g0)^2; sorted, and the doubled
+// eigenvalues of the embedding merged in pairs.
+__global__ void __launch_bounds__(1024) kry_final_kernel(JacBufs J, int m,
+                                                         const double* __restrict__ g0,
+                                                         const int* __restrict__ rank,
+                                                         double* __restrict__ d,
+                                                         double* __restrict__ wk,
+                                                         double* __restrict__ poles,
+                                                         double* __restrict__ weights,
+                                                         int32_t* __restrict__ rank_out) {
+    const double* E = J.A[*J.res];
+    const double* V = J.V[*J.res];
+    const int r = *rank, n = m / 2;
     for (int k = threadIdx.x; k < r; k += blockDim.x) {
         double s = 0.0;
-        for (int q = 0; q < r; ++q) s += V[(size_t)q * r + k] * w[q];
-        cs[k] = s * s;
-        d[k] = E[(size_t)k * r + k];
+        for (int q = 0; q < r; ++q) s += V[(size_t)q * m + k] * g0[q];
+        wk[k] = s * s;
+        d[k] = E[(size_t)k * m + k];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        // sort ascending (insertion sort, r <= 1024), then merge the pairs
         for (int i = 1; i < r; ++i) {
-            double dv = d[i], wv = cs[i];
+            const double dv = d[i], wv = wk[i];
             int j = i - 1;
             while (j >= 0 && d[j] > dv) {
                 d[j + 1] = d[j];
-                cs[j + 1] = cs[j];
+                wk[j + 1] = wk[j];
                 --j;
             }
             d[j + 1] = dv;
-            cs[j + 1] = wv;
+            wk[j + 1] = wv;
         }
         for (int k = 0; k < n; ++k) {
             if (2 * k + 1 < r) {
                 poles[k] = 0.5 * (d[2 * k] + d[2 * k + 1]);
-                weights[k] = cs[2 * k] + cs[2 * k + 1];
+                weights[k] = wk[2 * k] + wk[2 * k + 1];
             } else {
                 poles[k] = 0.0;
                 weights[k] = 0.0;
@@ -345,6 +423,8 @@ __global__ void __launch_bounds__(1024) krylov_kernel(const double* __restrict__
     }
 }
 
+}  // namespace
+
 extern "C" cr_status cheb_krylov(cr_ctx* ctx, const double* G, const double* H, int Nm,
                                  double cutoff, int n_out, double* mu_corr_out, double* poles_out,
                                  double* weights_out, int32_t* rank_out) {
@@ -352,8 +432,12 @@ extern "C" cr_status cheb_krylov(cr_ctx* ctx, const double* G, const double* H, 
     CR_CHECK_ARG(Nm >= 1 && Nm <= 512, "cheb_krylov: Nm=%d outside [1, 512]", Nm);
     CR_CHECK_ARG(n_out >= 1, "cheb_krylov: n_out < 1");
     CR_CHECK_ARG(G && H && mu_corr_out && poles_out && weights_out, "cheb_krylov: null array");
-    const size_t m = 2 * (size_t)Nm;
-    const size_t need = 4 * m * m + 3 * m + 8 * (size_t)Nm;
+    const int n = Nm, m = 2 * Nm;
+    const size_t mm = (size_t)m * m;
+    // workspace (doubles): A0, A1, V0, V1, X, C [m*m]; Y [m*n]; d, wk, g0 [m];
+    // 4 complex vectors [n]; norm shares [2 NORM_GRID]; ints: keep [m], rank, res, flag
+    const size_t need = 6 * mm + (size_t)m * n + 3 * (size_t)m + 8 * (size_t)n +
+                        2 * NORM_GRID + ((size_t)m + 3 + 1) / 2 + 1;
     if (ctx->kry_len < need) {
         // first use at this size: the only allocation outside cr_create
         if (ctx->kry) cudaFree(ctx->kry);
@@ -363,7 +447,50 @@ extern "C" cr_status cheb_krylov(cr_ctx* ctx, const double* G, const double* H, 
             return cr_fail(ctx, CR_ENOMEM, "cheb_krylov: workspace");
         ctx->kry_len = need;
     }
-    CR_LAUNCH(ctx, CR_K_OTHER, krylov_kernel<<<1, 1024, 0, ctx->stream>>>(G, H, Nm, cutoff, n_out, ctx->kry, mu_corr_out,
-                                               poles_out, weights_out, rank_out));
-    return cr_check_launch(ctx, "krylov_kernel");
+    double* w = ctx->kry;
+    JacBufs J;
+    J.A[0] = w;
+    J.A[1] = w + mm;
+    J.V[0] = w + 2 * mm;
+    J.V[1] = w + 3 * mm;
+    double* X = w + 4 * mm;
+    double* C = w + 5 * mm;
+    double* Y = w + 6 * mm;
+    double* d = Y + (size_t)m * n;
+    double* wk = d + m;
+    double* g0 = wk + m;
+    double* vec = g0 + m;
+    double* part = vec + 8 * (size_t)n;
+    int* keep = (int*)(part + 2 * NORM_GRID);
+    int* rank = keep + m;
+    J.res = rank + 1;
+    J.flag = rank + 2;
+    const unsigned gm = (unsigned)((mm + 255) / 256);
+    const unsigned gn = (unsigned)(((size_t)n * n + 255) / 256);
+    const dim3 g16((m + 15) / 16, (m + 15) / 16);
+    cudaStream_t st = ctx->stream;
+    // 1. G through its embedding: eigenvalues, kept rank, pseudo-inverse
+    cudaError_t e = cudaMemsetAsync(J.A[0], 0, mm * sizeof(double), st);
+    if (e != cudaSuccess) return cr_fail(ctx, CR_ECUDA, "cheb_krylov: %s", cudaGetErrorString(e));
+    CR_LAUNCH(ctx, CR_K_OTHER, kry_embed_kernel<<<gn, 256, 0, st>>>(G, n, J.A[0]));
+    jacobi_launch(ctx, J, m, part);
+    CR_LAUNCH(ctx, CR_K_OTHER, kry_keep_kernel<<<1, 1, 0, st>>>(J, m, cutoff, d, keep, rank));
+    CR_LAUNCH(ctx, CR_K_OTHER,
+              kry_pinv_kernel<<<(unsigned)(((size_t)m * n + 255) / 256), 256, 0, st>>>(J, m, d, keep, rank, Y));
+    // 2. corrected moments
+    CR_LAUNCH(ctx, CR_K_OTHER, kry_moments_kernel<<<1, 1024, 0, st>>>(G, H, n, Y, n_out, vec, mu_corr_out));
+    // 3. projected eigenproblem: X = V_kept d^-1/2 (zero-padded to m columns),
+    //    Hx = X^T Hemb X, diagonalised by the same Jacobi (padding stays zero)
+    CR_LAUNCH(ctx, CR_K_OTHER, kry_x_kernel<<<gm, 256, 0, st>>>(J, m, d, keep, rank, X));
+    CR_LAUNCH(ctx, CR_K_OTHER, kry_g0_kernel<<<(m + 255) / 256, 256, 0, st>>>(G, X, m, g0));
+    e = cudaMemsetAsync(C, 0, mm * sizeof(double), st);
+    if (e != cudaSuccess) return cr_fail(ctx, CR_ECUDA, "cheb_krylov: %s", cudaGetErrorString(e));
+    CR_LAUNCH(ctx, CR_K_OTHER, kry_embed_kernel<<<gn, 256, 0, st>>>(H, n, C));
+    CR_LAUNCH(ctx, CR_K_OTHER, kry_gemm_kernel<false><<<g16, dim3(16, 16), 0, st>>>(C, X, m, J.A[1]));
+    CR_LAUNCH(ctx, CR_K_OTHER, kry_gemm_kernel<true><<<g16, dim3(16, 16), 0, st>>>(X, J.A[1], m, C));
+    CR_LAUNCH(ctx, CR_K_OTHER, kry_sym_kernel<<<gm, 256, 0, st>>>(C, m, J.A[0]));
+    jacobi_launch(ctx, J, m, part);
+    CR_LAUNCH(ctx, CR_K_OTHER,
+              kry_final_kernel<<<1, 1024, 0, st>>>(J, m, g0, rank, d, wk, poles_out, weights_out, rank_out));
+    return cr_check_launch(ctx, "cheb_krylov");
 }
