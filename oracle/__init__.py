@@ -32,6 +32,9 @@ equations in the paper's order; library primitives (matrix products,
   spectrum  -- the spectral function on a frequency grid: Chebyshev sum
                with Jackson damping (Secs. II, V) and the continued
                fraction of the Krylov projection (Sec. IV).
+  groundstate -- ground-state preparation by natural-gradient energy
+               descent (Sec. I) with the metric S of Sec. III.
 """
 
-from . import lattice, philox, rbm, sampler, target, sr, exact, chebyshev, krylov, spectrum  # noqa: F401
+from . import (lattice, philox, rbm, sampler, target, sr, exact, chebyshev, krylov,  # noqa: F401
+               spectrum, groundstate)
