@@ -90,6 +90,15 @@ typedef enum {
                                Cheaper, but its error can make S + shift I
                                indefinite at small shifts (CR_ESINGULAR). */
 
+/* Modes of sr_step.  CR_SR_FIT: the projection fit of Sec. III (R = phi/psi,
+   F = dgamma gamma cot gamma (<O* R>/<R> - <O*>)).  CR_SR_ENERGY: ground-state
+   preparation (Sec. I: minimise <H>), R = the local energy (H psi)/psi in any
+   affine units (e.g. cheb_local_target with n = 1, prev = psi, beta = 1 gives
+   the local H'), F = -dgamma (<O* R> - <O*> <R>), dgamma the learning rate;
+   stats [0] is then 0. */
+#define CR_SR_FIT 0
+#define CR_SR_ENERGY 1
+
 /* Solvers for sr_step. */
 #define CR_SOLVE_CHOLESKY 0 /* explicit S and a direct solve (needs CR_CTX_EXPLICIT_S):
                                float64 contexts with P <= 2048 factor S in float64 in one
@@ -157,6 +166,7 @@ typedef struct {
     int cg_maxit;           /* CG iteration limit (CG only) */
     double cg_tol;          /* CG stops when |r| <= cg_tol |F| */
     int cg_precond;         /* 0: plain CG; 1: Jacobi preconditioner diag(S) + shift */
+    int mode;               /* CR_SR_FIT (Sec. III fit) or CR_SR_ENERGY (ground state) */
 } cr_sr_opts;
 
 /* ---------------------------------------------------------------- context */

@@ -18,6 +18,8 @@ FP64, FP32, MIXED = 0, 1, 2
 SOLVE_CHOLESKY, SOLVE_CG = 0, 1
 CTX_EXPLICIT_S = 1
 CTX_S_BF16X3 = 2
+SR_FIT = 0
+SR_ENERGY = 1
 STATS_LEN = 8
 STATUS = {0: "CR_OK", 1: "CR_EINVAL", 2: "CR_ENOMEM", 3: "CR_ECUDA", 4: "CR_ETIMEOUT",
           5: "CR_ENOTCONV", 6: "CR_ESINGULAR", 7: "CR_ENONFINITE"}
@@ -56,7 +58,7 @@ class Target(ctypes.Structure):
 class SROpts(ctypes.Structure):
     _fields_ = [("dgamma", ctypes.c_double), ("shift", ctypes.c_double),
                 ("solver", ctypes.c_int), ("cg_maxit", ctypes.c_int),
-                ("cg_tol", ctypes.c_double), ("cg_precond", ctypes.c_int)]
+                ("cg_tol", ctypes.c_double), ("cg_precond", ctypes.c_int), ("mode", ctypes.c_int)]
 
 
 _lib = None
@@ -286,7 +288,7 @@ class Context:
         return grad_params
 
     def sr_step(self, params, spins, tanh_theta, R, dgamma, shift, solver=SOLVE_CG, cg_maxit=100,
-                cg_tol=1e-6, stats_out=None, jacobi=False):
+                cg_tol=1e-6, stats_out=None, jacobi=False, mode=0):
         B = self._spins(spins)
         self._c(params, (self.P,), "params")
         self._c(tanh_theta, (B, self.M), "tanh_theta")
@@ -294,7 +296,7 @@ class Context:
         if stats_out is not None and not (stats_out.dtype == torch.float64 and stats_out.is_cuda
                                           and stats_out.numel() >= STATS_LEN):
             raise ValueError("stats_out: need a CUDA float64 tensor of 8 entries")
-        o = SROpts(dgamma, shift, solver, cg_maxit, cg_tol, 1 if jacobi else 0)
+        o = SROpts(dgamma, shift, solver, cg_maxit, cg_tol, 1 if jacobi else 0, int(mode))
         self._check(self.lib.sr_step(self.h, _ptr(params), _ptr(spins), _ptr(tanh_theta), _ptr(R),
                                      B, ctypes.byref(o), _ptr(stats_out)), "sr_step")
 

@@ -299,8 +299,10 @@ __device__ void force_scalars(const cpx<double>* redR, int P, int B, double dgam
     *cc = dgamma * (*gamma < 1e-8 ? 1.0 : *gamma / tan(*gamma));
 }
 
+// mode CR_SR_FIT: F = dgamma gamma cot gamma (<O* R>/<R> - <O*>) (Sec. III);
+// mode CR_SR_ENERGY: F = -dgamma (<O* R> - <O*> <R>), R the local energy.
 __global__ void force_kernel(const double* __restrict__ redR_, const double* __restrict__ redO_,
-                             int P, int B, double dgamma, double* __restrict__ F_,
+                             int P, int B, double dgamma, int mode, double* __restrict__ F_,
                              double* __restrict__ stats, int* __restrict__ status) {
     const cpx<double>* redR = (const cpx<double>*)redR_;
     const cpx<double>* redO = (const cpx<double>*)redO_;
@@ -310,14 +312,19 @@ __global__ void force_kernel(const double* __restrict__ redR_, const double* __r
     const double inv = 1.0 / B;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < P) {
-        cpx<double> f = cdiv(inv * redR[k], mR) - conj(inv * redO[k]);
-        ((cpx<double>*)F_)[k] = cc * f;
+        cpx<double> f;
+        if (mode == CR_SR_ENERGY)
+            f = -dgamma * (inv * redR[k] - conj(inv * redO[k]) * mR);
+        else
+            f = cc * (cdiv(inv * redR[k], mR) - conj(inv * redO[k]));
+        ((cpx<double>*)F_)[k] = f;
     }
     if (k == 0) {
-        if (!isfinite(mR.x) || !isfinite(mR.y) || !isfinite(mRR) || abs2(mR) == 0.0)
-            set_status(status, CR_ENONFINITE);
+        const bool bad = !isfinite(mR.x) || !isfinite(mR.y) || !isfinite(mRR) ||
+                         (mode != CR_SR_ENERGY && abs2(mR) == 0.0);
+        if (bad) set_status(status, CR_ENONFINITE);
         if (stats) {
-            stats[0] = gamma;
+            stats[0] = mode == CR_SR_ENERGY ? 0.0 : gamma;
             stats[1] = mR.x;
             stats[2] = mR.y;
             stats[3] = mRR;
@@ -681,8 +688,8 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
     if (s != CR_OK) return s;
     s = oreduce(c, false, spins, T, nullptr, B, redO, nullptr);
     if (s != CR_OK) return s;
-    CR_LAUNCH(c, CR_K_OTHER, force_kernel<<<(P + 255) / 256, 256, 0, c->stream>>>(redR, redO, P, B, o->dgamma, c->F, stats,
-                                                          c->d_status));
+    CR_LAUNCH(c, CR_K_OTHER, force_kernel<<<(P + 255) / 256, 256, 0, c->stream>>>(
+                                 redR, redO, P, B, o->dgamma, o->mode, c->F, stats, c->d_status));
     if ((s = cr_check_launch(c, "force_kernel")) != CR_OK) return s;
     double* x = c->cg;
     const bool blocked = o->solver == CR_SOLVE_CHOLESKY && chol_blocked(c);
@@ -745,6 +752,7 @@ extern "C" cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, con
                  "sr_step: unknown solver");
     CR_CHECK_ARG(opts->solver != CR_SOLVE_CHOLESKY || (ctx->flags & CR_CTX_EXPLICIT_S),
                  "sr_step: Cholesky needs a context created with CR_CTX_EXPLICIT_S");
+    CR_CHECK_ARG(opts->mode == CR_SR_FIT || opts->mode == CR_SR_ENERGY, "sr_step: unknown mode");
     CR_CHECK_ARG(opts->solver != CR_SOLVE_CG || (opts->cg_maxit >= 1 && opts->cg_tol >= 0.0 &&
                                                  (opts->cg_precond == 0 || opts->cg_precond == 1)),
                  "sr_step: bad CG options");
