@@ -34,7 +34,9 @@ equations in the paper's order; library primitives (matrix products,
                fraction of the Krylov projection (Sec. IV).
   groundstate -- ground-state preparation by natural-gradient energy
                descent (Sec. I) with the metric S of Sec. III.
+  symmetry  -- translation and rotation projection of the local sequence
+               onto every momentum of the square lattice (Appendix A).
 """
 
 from . import (lattice, philox, rbm, sampler, target, sr, exact, chebyshev, krylov,  # noqa: F401
-               spectrum, groundstate)
+               spectrum, groundstate, symmetry)

@@ -1,0 +1,72 @@
+"""Symmetry-projected Chebyshev states of the square lattice (Appendix A).
+
+The sequence is computed once for the local probe S^z_00; every momentum
+k = 2 pi (k1, k2) / L follows from translations T_m and 90-degree
+rotations R about site (0, 0):
+    |t~_nk> = L P_k^(T) P^(R) |t_n00>,
+    P_k^(T) = L^-2 sum_m e^{-i 2pi k.m / L} T_m,
+    P^(R)   = (1 + T_(1,0) R + T_(1,1) R^2 + T_(0,1) R^3) / 4.
+Operators act on basis states by moving spins: (T_m sigma)(x) = sigma(x - m),
+(R sigma)(x) = sigma(R^-1 x) with R (x, y) = (-y, x) mod L.  Then
+    B_{n,m,r}(s) = <s| T_m R^r |t_n00> / <s|psi> = t_n00(s') / psi(s),
+    s'(x) = s(R^r x + m),
+and, with the rotation terms of P^(R) folded into the translation sum,
+    B~_nk(s) = L^-1 sum_m e^{-i 2pi k.m / L} (1/4) [B_{n,m,0} + B_{n,m+(1,0),1}
+               + B_{n,m+(1,1),2} + B_{n,m+(0,1),3}].
+The Gram matrix of each momentum is G^(k)_nn' = < conj(B~_nk) B~_n'k > over
+samples of |psi|^2 (= <t~_nk|t~_n'k> / <psi|psi>).
+
+THIS MODULE IS TEST INFRASTRUCTURE (see the package docstring).
+"""
+
+import numpy as np
+
+from . import rbm
+
+SHIFTS = ((0, 0), (1, 0), (1, 1), (0, 1))  # translation paired with R^r in P^(R)
+
+
+def rotate(x, y, r, L):
+    """R^r (x, y) with R (x, y) = (-y, x) mod L."""
+    for _ in range(r % 4):
+        x, y = (-y) % L, x % L
+    return x, y
+
+
+def transform(spins, m, r, L):
+    """Rows s'(x) = s(R^r x + m) of the configurations in spins [B, L*L]."""
+    spins = np.asarray(spins)
+    out = np.empty_like(spins)
+    for y in range(L):
+        for x in range(L):
+            rx, ry = rotate(x, y, r, L)
+            src = ((rx + m[0]) % L) + L * ((ry + m[1]) % L)
+            out[:, x + L * y] = spins[:, src]
+    return out
+
+
+def b_tilde(params_list, N, M, L, spins, logpsi_ref):
+    """B~_nk(s) for every stored state n and momentum k: complex [Nm, L*L, B]
+    (momentum index k1 + L k2)."""
+    spins = np.asarray(spins, dtype=np.int8)
+    Bn = spins.shape[0]
+    out = np.zeros((len(params_list), L * L, Bn), dtype=np.complex128)
+    ks = [(k1, k2) for k2 in range(L) for k1 in range(L)]
+    for n, p in enumerate(params_list):
+        for m1 in range(L):
+            for m2 in range(L):
+                acc = np.zeros(Bn, dtype=np.complex128)
+                for r, (d1, d2) in enumerate(SHIFTS):
+                    sp = transform(spins, ((m1 + d1) % L, (m2 + d2) % L), r, L)
+                    acc = acc + 0.25 * np.exp(rbm.logpsi(p, N, M, sp) - logpsi_ref)
+                for ki, (k1, k2) in enumerate(ks):
+                    ph = np.exp(-2j * np.pi * (k1 * m1 + k2 * m2) / L) / L
+                    out[n, ki] += ph * acc
+    return out
+
+
+def gram_by_momentum(Bt, weights=None):
+    """G^(k)_nn' = < conj(B~_nk) B~_n'k >: complex [L*L, Nm, Nm]."""
+    Nm, Nk, Bn = Bt.shape
+    w = np.full(Bn, 1.0 / Bn) if weights is None else np.asarray(weights)
+    return np.einsum("nks,mks,s->knm", np.conj(Bt), Bt, w)

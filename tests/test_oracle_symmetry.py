@@ -1,0 +1,94 @@
+"""Pins for the symmetry projection (Appendix A): the estimator of the
+projected Gram matrices against the projected dense vectors built from the
+operator definitions, projector identities, and a state that is already
+symmetric."""
+
+import numpy as np
+import pytest
+
+from oracle import exact, rbm, symmetry
+
+
+def _perm_op(basis, L, f):
+    """Permutation matrix of the operator that maps configuration sigma to
+    sigma' with sigma'(x) = sigma(f(x)) (as a basis-index map)."""
+    index = {b.tobytes(): k for k, b in enumerate(basis)}
+    src = [f(x, y) for y in range(L) for x in range(L)]
+    dst = np.array([index[b[[sx + L * sy for sx, sy in src]].tobytes()] for b in basis])
+    return dst
+
+
+def _apply(dst, v):
+    # (A v)[dst[k]] = v[k]: A moves the amplitude of basis state k to dst[k]
+    out = np.zeros_like(v)
+    out[dst] = v
+    return out
+
+
+def test_projected_gram_equals_dense_projection():
+    L, M = 4, 6
+    N = L * L
+    basis = exact.sector_basis(N)
+    rng = np.random.default_rng(3)
+    psi_p = rbm.init_params(rng, N, M, 0.2)
+    states = [rbm.init_params(rng, N, M, 0.2) for _ in range(3)]
+    psi = exact.rbm_vector(psi_p, N, M, basis)
+    Z = np.vdot(psi, psi).real
+    # operators on states: (T_m v)(sigma) = v(T_m^-1 sigma): T_m moves the spin at
+    # x - m to x, i.e. maps sigma to sigma'(x) = sigma(x - m)
+    def T(m):
+        return _perm_op(basis, L, lambda x, y: ((x - m[0]) % L, (y - m[1]) % L))
+    Rop = _perm_op(basis, L, lambda x, y: symmetry.rotate(x, y, -1, L))  # sigma'(x) = sigma(R^-1 x)
+    def proj(v, k):
+        # L P_k^(T) P^(R) v
+        vr = v.copy()
+        acc = 0.25 * v
+        for r, sh in enumerate(symmetry.SHIFTS[1:], start=1):
+            vr = _apply(Rop, vr)                 # R^r v
+            acc = acc + 0.25 * _apply(T(sh), vr)
+        out = np.zeros_like(v)
+        for m1 in range(L):
+            for m2 in range(L):
+                ph = np.exp(-2j * np.pi * (k[0] * m1 + k[1] * m2) / L)
+                out = out + ph * _apply(T((m1, m2)), acc)
+        return out / L
+    dense = [exact.rbm_vector(p, N, M, basis) for p in states]
+    Bt = symmetry.b_tilde(states, N, M, L, basis, rbm.logpsi(psi_p, N, M, basis))
+    G = symmetry.gram_by_momentum(Bt, weights=np.abs(psi) ** 2 / Z)
+    for k in ((0, 0), (1, 0), (2, 1), (2, 2), (3, 1)):
+        ki = k[0] + L * k[1]
+        tk = [proj(v, k) for v in dense]
+        Gd = np.array([[np.vdot(a, b) for b in tk] for a in tk]) / Z
+        assert np.allclose(G[ki], Gd, atol=1e-12 * np.abs(Gd).max()), k
+        # B~ is the amplitude ratio of the projected state: <s|t~_nk> / <s|psi>
+        assert np.allclose(Bt[0, ki] * psi, tk[0], atol=1e-12 * np.abs(tk[0]).max())
+
+
+def test_momentum_sum_and_symmetric_state():
+    L, M = 4, 4
+    N = L * L
+    basis = exact.sector_basis(N)[:300]
+    rng = np.random.default_rng(5)
+    p = rbm.init_params(rng, N, M, 0.3)
+    lref = rbm.logpsi(p, N, M, basis)
+    Bt = symmetry.b_tilde([p], N, M, L, basis, lref)
+    # sum_k L P_k = L: the momenta add up to L times the rotation average at m = 0
+    rot = sum(0.25 * np.exp(rbm.logpsi(p, N, M, symmetry.transform(basis, sh, r, L)) - lref)
+              for r, sh in enumerate(symmetry.SHIFTS))
+    assert np.allclose(Bt[0].sum(axis=0), L * rot, atol=1e-12)
+    # an RBM with W = 0 and uniform a, b is invariant under every lattice map:
+    # only k = 0 survives, with B~ = L
+    q = np.zeros(rbm.n_params(N, M), dtype=np.complex128)
+    q[:N] = 0.1 + 0.2j
+    q[N:N + M] = -0.3 + 0.1j
+    Bq = symmetry.b_tilde([q], N, M, L, basis, rbm.logpsi(q, N, M, basis))
+    assert np.allclose(Bq[0, 0], L)
+    assert np.allclose(Bq[0, 1:], 0, atol=1e-12)
+
+
+def test_rotation_is_a_quarter_turn():
+    L = 5
+    assert symmetry.rotate(1, 0, 1, L) == (0, 1)
+    assert symmetry.rotate(1, 2, 4, L) == (1, 2)
+    s = np.arange(L * L)[None, :]
+    assert np.array_equal(symmetry.transform(symmetry.transform(s, (0, 0), 1, L), (0, 0), 3, L), s)
