@@ -308,6 +308,27 @@ cr_status logpsi_backward_noalloc(int N, int M, cr_prec prec, const int8_t* spin
 cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, const void* tanh_theta,
                   const void* R, int B, const cr_sr_opts* opts, double* stats_out);
 
+/* Appendix A: symmetry projection of one Chebyshev sequence, computed for
+   the local probe S^z_00, onto every momentum of the L x L square lattice
+   (the context's lattice must be square).  For each sample s of |psi|^2 and
+   each stored state t_n (plain RBM states, no probe factor):
+     B~_nk(s) = L^-1 sum_m e^{-i 2 pi k.m / L} (1/4) sum_{r=0..3}
+                t_n(s'_{m,r}) / psi(s),   s'_{m,r}(x) = s(R^r x + m + d_r),
+   R (x, y) = (-y, x) mod L, d_r = (0,0), (1,0), (1,1), (0,1) (the
+   translation paired with R^r in the rotation projector), i.e. the amplitude
+   ratio of L P_k^(T) P^(R) |t_n>.  states: host array of Nm cr_state;
+   spins int8 [B][N]; logpsi_ref: log psi at the samples (context precision
+   complex [B]); Bt_out: context precision complex [L*L][Nm][B], momentum
+   index k1 + L k2, so that row block k is the Bmat of cheb_gram for that
+   momentum (G^(k)_nn' = <conj(B~_nk) B~_n'k>; mu_nk = G^(k)_0n).
+   workspace: caller-owned device memory of sym_workspace_bytes(ctx, B)
+   bytes (4 N B N bytes of transformed configurations and two complex
+   arrays); the call allocates nothing. */
+size_t sym_workspace_bytes(const cr_ctx* ctx, int B);
+cr_status sym_btilde(cr_ctx* ctx, const cr_state* states, int Nm, const int8_t* spins,
+                     const void* logpsi_ref, int B, void* workspace, size_t workspace_bytes,
+                     void* Bt_out);
+
 /* Sec. II, Eq. (Aw), with the Jackson damping of Sec. V: the spectral
    function on a frequency grid from the moments mu_n, n = 0 .. Nm - 1,
      A(omega) = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n T_n(omega')]
@@ -353,7 +374,7 @@ cr_status cheb_moment(cr_ctx* ctx, const cr_state* state, const double* beta, do
 /* Sec. IV estimators: G_nm = <conj(B_n) B_m>, H_nm = <conj(B_n) HB_m>, then
    H <- (H + H^dag)/2. Bmat, HBmat complex [Nm][ld] (row n = column B_n over
    the B samples, leading dimension ld >= B); G_out, H_out complex128
-   [Nm][Nm] (device). */
+   [Nm][Nm] (device).  HBmat and H_out may both be NULL (G only). */
 cr_status cheb_gram(cr_ctx* ctx, const void* Bmat, const void* HBmat, int Nm, int B, int ld,
                     double* G_out, double* H_out);
 

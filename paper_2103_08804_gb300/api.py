@@ -30,7 +30,7 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cheb_local_target", "logderiv", "logpsi_backward", "sr_step", "cheb_moment",
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
            "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix",
-           "cheb_spectrum", "cheb_lorentzian")
+           "cheb_spectrum", "cheb_lorentzian", "sym_workspace_bytes", "sym_btilde")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
           "chol": 7, "trsv": 8}
 
@@ -100,12 +100,15 @@ def load(path=None):
     lib.cr_set_chunks.argtypes = [vp, i]
     lib.sr_smatrix.argtypes = [vp, vp, vp, i, d, vp]
     lib.cheb_spectrum.argtypes = [vp, vp, i, d, d, i, vp, i, vp]
+    lib.sym_workspace_bytes.argtypes = [vp, i]
+    lib.sym_workspace_bytes.restype = ctypes.c_size_t
+    lib.sym_btilde.argtypes = [vp, ctypes.POINTER(State), i, vp, vp, i, vp, ctypes.c_size_t, vp]
     lib.cheb_lorentzian.argtypes = [vp, vp, vp, i, d, d, d, vp, i, vp]
     lib.cr_max_chunks.argtypes = [vp]
     lib.logpsi_backward_noalloc.argtypes = [i, i, i, vp, vp, i, vp, vp, vp, ctypes.c_char_p, i]
     for f in SYMBOLS:
         if f not in ("cr_last_error", "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds",
-                     "cr_n_launches", "cr_max_chunks"):
+                     "cr_n_launches", "cr_max_chunks", "sym_workspace_bytes"):
             getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -313,6 +316,24 @@ class Context:
                                         _ptr(S_out)), "sr_smatrix")
         return S_out
 
+    def sym_btilde(self, params, spins, logpsi_ref, workspace=None):
+        """Appendix A: B~_nk(s) for the stored states params [Nm, P] (plain
+        RBMs) at the samples; returns [L*L, Nm, B] (momentum k1 + L k2)."""
+        B = self._spins(spins)
+        self._c(logpsi_ref, (B,), "logpsi_ref")
+        Nm = params.shape[0]
+        if params.dtype != self.cdtype or tuple(params.shape) != (Nm, self.P) \
+                or not params.is_contiguous():
+            raise ValueError("params: contiguous [Nm, P] in the context precision")
+        need = int(self.lib.sym_workspace_bytes(self.h, B))
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device=spins.device)
+        sts = (State * Nm)(*[self.state(params[n]) for n in range(Nm)])
+        out = torch.empty(self.N, Nm, B, dtype=self.cdtype, device=spins.device)
+        self._check(self.lib.sym_btilde(self.h, sts, Nm, _ptr(spins), _ptr(logpsi_ref), B,
+                                        _ptr(workspace), need, _ptr(out)), "sym_btilde")
+        return out
+
     def cheb_spectrum(self, mu, a, Wp, omega, jackson=True):
         """A(omega) of Eq. (Aw) (complex128 [len(omega)]) from the moments mu."""
         for t, name in ((mu, "mu"), (omega, "omega")):
@@ -354,12 +375,14 @@ class Context:
                                          _ptr(HBcol), _ptr(mu_out)), "cheb_moment")
 
     def cheb_gram(self, Bmat, HBmat, G_out, H_out, n_samples=None):
+        """HBmat and H_out may both be None (G only)."""
         Nm, ld = Bmat.shape
         B = ld if n_samples is None else n_samples
         self._c(Bmat, (Nm, ld), "Bmat")
         self._c(HBmat, (Nm, ld), "HBmat")
         for t in (G_out, H_out):
-            if not (t.dtype == torch.complex128 and t.is_cuda and tuple(t.shape) == (Nm, Nm)):
+            if t is not None and not (t.dtype == torch.complex128 and t.is_cuda
+                                      and tuple(t.shape) == (Nm, Nm)):
                 raise ValueError("G_out / H_out: need CUDA complex128 [Nm, Nm]")
         self._check(self.lib.cheb_gram(self.h, _ptr(Bmat), _ptr(HBmat), Nm, B, ld, _ptr(G_out),
                                        _ptr(H_out)), "cheb_gram")

@@ -22,7 +22,8 @@ __global__ void gram_kernel(const cpx<R>* __restrict__ Bm, const cpx<R>* __restr
         tn[threadIdx.y][threadIdx.x] = (nn < Nm && s < B) ? Bm[(size_t)nn * ld + s] : cpx<R>{R(0), R(0)};
         const int mm = blockIdx.x * 16 + threadIdx.y;
         tm[threadIdx.y][threadIdx.x] = (mm < Nm && s < B) ? Bm[(size_t)mm * ld + s] : cpx<R>{R(0), R(0)};
-        th[threadIdx.y][threadIdx.x] = (mm < Nm && s < B) ? HBm[(size_t)mm * ld + s] : cpx<R>{R(0), R(0)};
+        th[threadIdx.y][threadIdx.x] =
+            (HBm && mm < Nm && s < B) ? HBm[(size_t)mm * ld + s] : cpx<R>{R(0), R(0)};
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
@@ -34,7 +35,7 @@ __global__ void gram_kernel(const cpx<R>* __restrict__ Bm, const cpx<R>* __restr
     }
     if (n < Nm && m < Nm) {
         ((cpx<double>*)G_)[(size_t)n * Nm + m] = (1.0 / B) * g;
-        ((cpx<double>*)H_)[(size_t)n * Nm + m] = (1.0 / B) * h;
+        if (H_) ((cpx<double>*)H_)[(size_t)n * Nm + m] = (1.0 / B) * h;
     }
 }
 
@@ -54,7 +55,8 @@ extern "C" cr_status cheb_gram(cr_ctx* ctx, const void* Bmat, const void* HBmat,
                                int ld, double* G_out, double* H_out) {
     if (!ctx) return CR_EINVAL;
     CR_CHECK_ARG(Nm >= 1 && B >= 1 && ld >= B, "cheb_gram: bad sizes");
-    CR_CHECK_ARG(Bmat && HBmat && G_out && H_out, "cheb_gram: null array");
+    CR_CHECK_ARG(Bmat && G_out && ((HBmat && H_out) || (!HBmat && !H_out)),
+                 "cheb_gram: null array (HBmat and H_out are both given or both NULL)");
     dim3 g((Nm + 15) / 16, (Nm + 15) / 16);
     if (ctx->prec == CR_FP64)
         CR_LAUNCH(ctx, CR_K_OTHER, gram_kernel<double><<<g, dim3(16, 16), 0, ctx->stream>>>(
@@ -62,7 +64,8 @@ extern "C" cr_status cheb_gram(cr_ctx* ctx, const void* Bmat, const void* HBmat,
     else
         CR_LAUNCH(ctx, CR_K_OTHER, gram_kernel<float><<<g, dim3(16, 16), 0, ctx->stream>>>(
             (const cpx<float>*)Bmat, (const cpx<float>*)HBmat, Nm, B, ld, G_out, H_out));
-    CR_LAUNCH(ctx, CR_K_OTHER, hermitise_kernel<<<(Nm * Nm + 255) / 256, 256, 0, ctx->stream>>>(H_out, Nm));
+    if (H_out)
+        CR_LAUNCH(ctx, CR_K_OTHER, hermitise_kernel<<<(Nm * Nm + 255) / 256, 256, 0, ctx->stream>>>(H_out, Nm));
     return cr_check_launch(ctx, "cheb_gram");
 }
 

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "chebrbm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^[a-z_ ]*?\b(?:cr_status|int|long long|const char\*)\s+(\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^[a-z_ ]*?\b(?:cr_status|int|long long|size_t|const char\*)\s+(\w+)\s*\(", src, flags=re.M)
     return set(names)
 
 

@@ -1,0 +1,51 @@
+"""Symmetry projection (Appendix A) through the C ABI against the oracle:
+B~_nk(s) for every momentum of a 4 x 4 lattice at sampled configurations
+(float64 to 1e-10, float32 to 1e-4 of the largest value), and the
+per-momentum Gram matrices through cheb_gram."""
+
+import numpy as np
+import pytest
+
+from gpu_common import dev, host, need_gpu, torch
+from oracle import rbm, symmetry
+from paper_2103_08804_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_btilde_and_momentum_grams_against_oracle(prec, tol):
+    from paper_2103_08804_gb300 import api
+    L, M, B, Nm = 4, 8, 517, 3
+    N = L * L
+    psi = synth.rbm_params(20, N, M, 0.2)
+    states = [synth.rbm_params(21 + n, N, M, 0.2) for n in range(Nm)]
+    spins = synth.sz0_spins(30, B, N)
+    lref = rbm.logpsi(psi, N, M, spins)
+    Bt_ref = symmetry.b_tilde(states, N, M, L, spins, lref)          # [Nm, N, B]
+    G_ref = symmetry.gram_by_momentum(Bt_ref)                          # [N, Nm, Nm]
+    cd = torch.complex128 if prec == 0 else torch.complex64
+    ctx = api.Context(L, L, M, B, prec=prec)
+    Bt = ctx.sym_btilde(dev(np.array(states), cd), dev(spins, torch.int8), dev(lref, cd))
+    Bh = host(Bt).astype(np.complex128)                                # [N, Nm, B]
+    scale = np.abs(Bt_ref).max()
+    assert np.max(np.abs(Bh - np.transpose(Bt_ref, (1, 0, 2)))) <= tol * scale
+    for k in (0, 1, 5, 10, 15):
+        G = torch.zeros(Nm, Nm, dtype=torch.complex128, device="cuda")
+        ctx.cheb_gram(Bt[k], None, G, None)
+        assert np.allclose(host(G), G_ref[k], rtol=0, atol=10 * tol * np.abs(G_ref).max()), k
+    ctx.sync_status()
+
+
+def test_btilde_rejects_chains_and_probe_states():
+    from paper_2103_08804_gb300 import api
+    ctx = api.Context(8, 1, 4, 16, prec=1)
+    p = torch.zeros(1, ctx.P, dtype=torch.complex64, device="cuda")
+    sp = dev(synth.sz0_spins(1, 16, 8), torch.int8)
+    with pytest.raises(api.CRError):
+        ctx.sym_btilde(p, sp, torch.zeros(16, dtype=torch.complex64, device="cuda"))
