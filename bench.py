@@ -80,31 +80,18 @@ def parse():
 
 
 def dist_setup():
-    import torch
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    return ws, rank, local
+    from paper_2103_08804_gb300 import replicas
+    return replicas.init()
 
 
 def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2103_08804_gb300 import replicas
+    replicas.barrier(ws)
 
 
 def max_over_ranks(ws, x):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2103_08804_gb300 import replicas
+    return replicas.max_over_ranks(ws, x)
 
 
 class ClockSampler:
@@ -245,13 +232,13 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD, cyc=CYCLE):
     """Time K moments of one precision path; returns (result dict, config, workload)."""
     import torch
 
-    from paper_2103_08804_gb300 import api, driver, synth
+    from paper_2103_08804_gb300 import api, driver, replicas, synth
 
     wl = synth.WORKLOADS[wl_name]
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
     K, W = args.steps, args.warmup
     n_moments = 1 + max(cyc)
-    seed = 1000 + 17 * rank
+    seed = replicas.replica_seed(1000, rank)
     prec = {"fp32": api.FP32, "mixed": api.MIXED}[prec_name]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -670,7 +657,7 @@ def run_explicit(args):
     """Explicit-S workload: one step = one moment with the Cholesky solve."""
     import torch
 
-    from paper_2103_08804_gb300 import api, driver, synth
+    from paper_2103_08804_gb300 import api, driver, replicas, synth
 
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -678,7 +665,7 @@ def run_explicit(args):
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
     K, W = args.steps, args.warmup
     n_moments = 1 + max(CYCLE)
-    seed = 2000 + 17 * rank
+    seed = replicas.replica_seed(2000, rank)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = api.Context(wl.Lx, wl.Ly, wl.M, wl.walkers, prec=api.MIXED, explicit_s=True,
@@ -822,7 +809,7 @@ def run_batch(args):
     """Momentum scan: every sequence advances one moment per step."""
     import torch
 
-    from paper_2103_08804_gb300 import api, batch, synth
+    from paper_2103_08804_gb300 import api, batch, replicas, synth
 
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -831,9 +818,10 @@ def run_batch(args):
     iters = 50 if args.iters is None else args.iters
     specs = batch.momentum_scan_specs(L=8, alpha=2, chains=(48, 96), walkers=8192,
                                       n_moments=n_moments, n_iter=iters, sigma=0.02,
-                                      seed=1000 + 17 * rank, n_therm=2, n_therm_ref=20,
+                                      seed=1000, n_therm=2, n_therm_ref=20,
                                       solver=api.SOLVE_CG, cg_maxit=args.cg_maxit,
                                       cg_tol=args.cg_tol, jacobi=args.jacobi)
+    specs = replicas.shard_specs(specs, rank, ws)  # sequence sharding: disjoint shares
     main = torch.cuda.Stream()
     torch.cuda.set_stream(main)
     t0 = time.perf_counter()
@@ -884,7 +872,7 @@ def run_batch(args):
             torch.cuda.synchronize()
             barrier(ws)
             ms = max_over_ranks(ws, float(np.mean([e[0].elapsed_time(e[1]) for e in ev])))
-            res[schedule] = {"ms_per_step": ms, "value": ws * n_seq * 3600.0 * 1000.0 / ms,
+            res[schedule] = {"ms_per_step": ms, "value": n_seq_all * 3600.0 * 1000.0 / ms,
                              "gpu_launches": int(launches)}
     clocks = clk.summary()
     for c in b.ctxs:
@@ -941,15 +929,17 @@ def run_batch(args):
         "config": {"workload": "momentum scan: 8x8 square lattice at its 15 irreducible q "
                                "(q=0 skipped: vanishing probe) + chains N=48 and N=96 at q=pi/2, "
                                "alpha=2, 8192 walkers each, one moment of every sequence per step",
-                   "sequences": n_seq, "skipped": b.skipped, "iters_per_moment": iters,
+                   "sequences": n_seq_all, "sequences_per_rank": n_seq, "skipped": b.skipped,
+                   "iters_per_moment": iters,
                    "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol,
                    "chunks": dict(zip([s.name for s in b.active], b.chunks)),
                    "autotune": tuned, "autotune_s": tune_s, "l2": "256 MiB buffer written between timed steps",
                    "launch": "one CUDA graph per iteration holding every sequence (forked streams)",
-                   "moments": BATCH_CYCLE_NOTE, "parallelism": f"replicas x{ws}"},
+                   "moments": BATCH_CYCLE_NOTE,
+                   "parallelism": f"sequences sharded over {ws} rank(s), no collective"},
         "gpu_launches": bt["gpu_launches"],
         "clocks": clocks,
-        "e2e": {"value": ws * n_seq * 3600.0 * 1000.0 / e2e_v, "unit": "moments/hour",
+        "e2e": {"value": n_seq_all * 3600.0 * 1000.0 / e2e_v, "unit": "moments/hour",
                 "h2d_bytes_per_step": Bi, "d2h_bytes_per_step": Bo},
         "roofline": roof,
         "per_q": pq,
