@@ -2,11 +2,12 @@
 //
 // cheb_gram builds sigma_nm = <t_n|t_m> and H_nm = <t_n|H'|t_m> from the
 // per-sample columns B_n(s) = t_n(s)/psi(s), (H' t_n)(s)/psi(s).
-// cheb_krylov then works in float64 on one CTA: a complex Hermitian n x n
-// matrix A = Ar + i Ai is handled through its real symmetric embedding
+// cheb_krylov then works in float64: a complex Hermitian n x n matrix
+// A = Ar + i Ai is handled through its real symmetric embedding
 // [[Ar, -Ai], [Ai, Ar]] (every eigenvalue twice, eigenvector pairs
 // [ur; ui], [-ui; ur]), diagonalised by cyclic Jacobi rotations applied to
-// n disjoint pairs at a time (round-robin ordering).
+// n disjoint pairs at a time (round-robin ordering), one launch per round on
+// many CTAs; the moment recursion runs on one CTA.
 #include "common.cuh"
 
 // ------------------------------------------------------------------ Gram

@@ -12,6 +12,9 @@
 //   ov_tc_kernel      u_s = sum_i sigma_si v_a_i + sum_j T_sj (v_b_j + (sigma V)_sj)
 //   oreduce_tc_kernel sum over a walker chunk of sigma_si conj(T_sj) g_s, plus
 //                     the a-, b- and scalar sums of oreduce_kernel's partial rows
+//
+// The explicit S of the Cholesky path (sgram_tc_kernel, further down) has
+// float32 values in both operands; both are split (see there).
 #include <cuda_bf16.h>
 
 #include <vector>
