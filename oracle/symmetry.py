@@ -16,12 +16,20 @@ and, with the rotation terms of P^(R) folded into the translation sum,
 The Gram matrix of each momentum is G^(k)_nn' = < conj(B~_nk) B~_n'k > over
 samples of |psi|^2 (= <t~_nk|t~_n'k> / <psi|psi>).
 
+The projected Hamiltonian H^(k) follows the same procedure.  H' = (H - E0)/a
+- W' commutes with every translation and rotation of the periodic lattice, so
+H' |t~_nk> = L P_k^(T) P^(R) H' |t_n00>, and
+    HB~_nk(s) = <s|H'|t~_nk> / <s|psi>
+is the projection above applied to (H' t_n00)(s') / psi(s) in place of
+t_n00(s') / psi(s); then H^(k)_nn' = < conj(B~_nk) HB~_n'k >
+(= <t~_nk|H'|t~_n'k> / <psi|psi>).
+
 THIS MODULE IS TEST INFRASTRUCTURE (see the package docstring).
 """
 
 import numpy as np
 
-from . import rbm
+from . import rbm, target
 
 SHIFTS = ((0, 0), (1, 0), (1, 1), (0, 1))  # translation paired with R^r in P^(R)
 
@@ -45,9 +53,9 @@ def transform(spins, m, r, L):
     return out
 
 
-def b_tilde(params_list, N, M, L, spins, logpsi_ref):
-    """B~_nk(s) for every stored state n and momentum k: complex [Nm, L*L, B]
-    (momentum index k1 + L k2)."""
+def _project(params_list, L, spins, value):
+    """L^-1 sum_m e^{-i 2pi k.m / L} (1/4) sum_r value(t_n, s'_{m + d_r, r})
+    for every state n and momentum k: complex [Nm, L*L, B]."""
     spins = np.asarray(spins, dtype=np.int8)
     Bn = spins.shape[0]
     out = np.zeros((len(params_list), L * L, Bn), dtype=np.complex128)
@@ -58,15 +66,32 @@ def b_tilde(params_list, N, M, L, spins, logpsi_ref):
                 acc = np.zeros(Bn, dtype=np.complex128)
                 for r, (d1, d2) in enumerate(SHIFTS):
                     sp = transform(spins, ((m1 + d1) % L, (m2 + d2) % L), r, L)
-                    acc = acc + 0.25 * np.exp(rbm.logpsi(p, N, M, sp) - logpsi_ref)
+                    acc = acc + 0.25 * value(p, sp)
                 for ki, (k1, k2) in enumerate(ks):
                     ph = np.exp(-2j * np.pi * (k1 * m1 + k2 * m2) / L) / L
                     out[n, ki] += ph * acc
     return out
 
 
-def gram_by_momentum(Bt, weights=None):
-    """G^(k)_nn' = < conj(B~_nk) B~_n'k >: complex [L*L, Nm, Nm]."""
+def b_tilde(params_list, N, M, L, spins, logpsi_ref):
+    """B~_nk(s) for every stored state n and momentum k: complex [Nm, L*L, B]
+    (momentum index k1 + L k2)."""
+    return _project(params_list, L, spins,
+                    lambda p, sp: np.exp(rbm.logpsi(p, N, M, sp) - logpsi_ref))
+
+
+def hb_tilde(params_list, N, M, L, J, E0, a, Wp, spins, logpsi_ref):
+    """HB~_nk(s) = <s|H'|t~_nk> / <s|psi> for every stored state n and
+    momentum k: complex [Nm, L*L, B], from (H' t_n00)(s') / psi(s) at every
+    transformed configuration (oracle.target.apply_hprime, no probe)."""
+    return _project(params_list, L, spins,
+                    lambda p, sp: target.apply_hprime(target.State(p), N, M, L, L, J, E0, a, Wp,
+                                                      (0.0, 0.0), sp, logpsi_ref))
+
+
+def gram_by_momentum(Bt, weights=None, HBt=None):
+    """G^(k)_nn' = < conj(B~_nk) B~_n'k >, or with HBt the projected
+    H^(k)_nn' = < conj(B~_nk) HB~_n'k >: complex [L*L, Nm, Nm]."""
     Nm, Nk, Bn = Bt.shape
     w = np.full(Bn, 1.0 / Bn) if weights is None else np.asarray(weights)
-    return np.einsum("nks,mks,s->knm", np.conj(Bt), Bt, w)
+    return np.einsum("nks,mks,s->knm", np.conj(Bt), Bt if HBt is None else HBt, w)

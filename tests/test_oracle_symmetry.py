@@ -1,6 +1,7 @@
-"""Pins for the symmetry projection (Appendix A): the estimator of the
-projected Gram matrices against the projected dense vectors built from the
-operator definitions, projector identities, and a state that is already
+"""Pins for the symmetry projection (Appendix A): the estimators of the
+projected Gram and Hamiltonian matrices against the projected dense vectors
+built from the operator definitions (and the dense H' of exact
+diagonalisation), projector identities, and a state that is already
 symmetric."""
 
 import numpy as np
@@ -25,6 +26,30 @@ def _apply(dst, v):
     return out
 
 
+def _dense_projector(basis, L):
+    """v -> L P_k^(T) P^(R) v on dense vectors over `basis`, from the
+    permutation operators themselves."""
+    # operators on states: (T_m v)(sigma) = v(T_m^-1 sigma): T_m moves the spin at
+    # x - m to x, i.e. maps sigma to sigma'(x) = sigma(x - m)
+    def T(m):
+        return _perm_op(basis, L, lambda x, y: ((x - m[0]) % L, (y - m[1]) % L))
+    Rop = _perm_op(basis, L, lambda x, y: symmetry.rotate(x, y, -1, L))  # sigma'(x) = sigma(R^-1 x)
+    Ts = {(m1, m2): T((m1, m2)) for m1 in range(L) for m2 in range(L)}
+
+    def proj(v, k):
+        vr = v.copy()
+        acc = 0.25 * v
+        for r, sh in enumerate(symmetry.SHIFTS[1:], start=1):
+            vr = _apply(Rop, vr)                 # R^r v
+            acc = acc + 0.25 * _apply(Ts[sh], vr)
+        out = np.zeros_like(v)
+        for (m1, m2), Tm in Ts.items():
+            ph = np.exp(-2j * np.pi * (k[0] * m1 + k[1] * m2) / L)
+            out = out + ph * _apply(Tm, acc)
+        return out / L
+    return proj
+
+
 def test_projected_gram_equals_dense_projection():
     L, M = 4, 6
     N = L * L
@@ -34,24 +59,7 @@ def test_projected_gram_equals_dense_projection():
     states = [rbm.init_params(rng, N, M, 0.2) for _ in range(3)]
     psi = exact.rbm_vector(psi_p, N, M, basis)
     Z = np.vdot(psi, psi).real
-    # operators on states: (T_m v)(sigma) = v(T_m^-1 sigma): T_m moves the spin at
-    # x - m to x, i.e. maps sigma to sigma'(x) = sigma(x - m)
-    def T(m):
-        return _perm_op(basis, L, lambda x, y: ((x - m[0]) % L, (y - m[1]) % L))
-    Rop = _perm_op(basis, L, lambda x, y: symmetry.rotate(x, y, -1, L))  # sigma'(x) = sigma(R^-1 x)
-    def proj(v, k):
-        # L P_k^(T) P^(R) v
-        vr = v.copy()
-        acc = 0.25 * v
-        for r, sh in enumerate(symmetry.SHIFTS[1:], start=1):
-            vr = _apply(Rop, vr)                 # R^r v
-            acc = acc + 0.25 * _apply(T(sh), vr)
-        out = np.zeros_like(v)
-        for m1 in range(L):
-            for m2 in range(L):
-                ph = np.exp(-2j * np.pi * (k[0] * m1 + k[1] * m2) / L)
-                out = out + ph * _apply(T((m1, m2)), acc)
-        return out / L
+    proj = _dense_projector(basis, L)
     dense = [exact.rbm_vector(p, N, M, basis) for p in states]
     Bt = symmetry.b_tilde(states, N, M, L, basis, rbm.logpsi(psi_p, N, M, basis))
     G = symmetry.gram_by_momentum(Bt, weights=np.abs(psi) ** 2 / Z)
@@ -62,6 +70,38 @@ def test_projected_gram_equals_dense_projection():
         assert np.allclose(G[ki], Gd, atol=1e-12 * np.abs(Gd).max()), k
         # B~ is the amplitude ratio of the projected state: <s|t~_nk> / <s|psi>
         assert np.allclose(Bt[0, ki] * psi, tk[0], atol=1e-12 * np.abs(tk[0]).max())
+
+
+def test_projected_hamiltonian_equals_dense_projection():
+    # 3 x 3 lattice, sector of 4 up-spins (126 states): the dense H' of exact
+    # diagonalisation applied to the projected dense vectors
+    L, M, J, E0, a, Wp = 3, 5, 1.0, -4.1, 3.7, 0.3
+    N = L * L
+    basis = exact.sector_basis(N, n_up=4)
+    rng = np.random.default_rng(11)
+    psi_p = rbm.init_params(rng, N, M, 0.3)
+    states = [rbm.init_params(rng, N, M, 0.3) for _ in range(3)]
+    psi = exact.rbm_vector(psi_p, N, M, basis)
+    Z = np.vdot(psi, psi).real
+    Hp = exact.rescaled(exact.hamiltonian(L, L, J, basis), E0, a, Wp)
+    proj = _dense_projector(basis, L)
+    lref = rbm.logpsi(psi_p, N, M, basis)
+    Bt = symmetry.b_tilde(states, N, M, L, basis, lref)
+    HBt = symmetry.hb_tilde(states, N, M, L, J, E0, a, Wp, basis, lref)
+    w = np.abs(psi) ** 2 / Z
+    H = symmetry.gram_by_momentum(Bt, weights=w, HBt=HBt)
+    dense = [exact.rbm_vector(p, N, M, basis) for p in states]
+    for k1 in range(L):
+        for k2 in range(L):
+            ki = k1 + L * k2
+            tk = [proj(v, (k1, k2)) for v in dense]
+            Hd = np.array([[np.vdot(u, Hp @ v) for v in tk] for u in tk]) / Z
+            assert np.allclose(H[ki], Hd, atol=1e-12 * np.abs(Hd).max()), (k1, k2)
+            assert np.allclose(H[ki], H[ki].conj().T, atol=1e-12 * np.abs(Hd).max())
+            # HB~ is the amplitude ratio of H' applied to the projected state
+            for n in range(len(states)):
+                assert np.allclose(HBt[n, ki] * psi, Hp @ tk[n],
+                                   atol=1e-12 * np.abs(Hp @ tk[n]).max()), (k1, k2, n)
 
 
 def test_momentum_sum_and_symmetric_state():
