@@ -9,7 +9,7 @@ then beta_n = <R> and mu_n with its Krylov columns.  Inputs are synthetic
 L2 is flushed between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload chain64|batch|square10|square16]
+                  [--workload chain64|batch|square10|square16|sym6]
 
 --workload batch times the momentum scan instead: all 15 irreducible momenta
 of an 8 x 8 square lattice (q = 0 has a vanishing probe and is skipped) plus
@@ -28,6 +28,10 @@ sample, for the default splits and for the cheaper two-term (bf16x3) form.
 tensor-core kernels cover M <= 256 only while their operands fit in shared
 memory), plus the Krylov step over 300 states (Gram estimators of 300
 sampled columns and the float64 generalized eigenproblem).
+
+--workload sym6 times the symmetry projection of Appendix A on the 6 x 6
+lattice (alpha = 2): B~ and HB~ of 150 stored states at 4096 samples for
+all 36 momenta, then G^(k) and H^(k) of every momentum.
 
 Prints one JSON line.  Under torchrun every rank runs an independent
 sequence (a different seed): weak scaling with no data-path collective.
@@ -73,7 +77,7 @@ def parse():
     ap.add_argument("--only-mixed", action="store_true",
                     help="chain64: skip the plain float32 path (tuning runs)")
     ap.add_argument("--workload", default="chain64",
-                    choices=["chain64", "batch", "square10", "square16"])
+                    choices=["chain64", "batch", "square10", "square16", "sym6"])
     ap.add_argument("--s-error-walkers", type=int, default=2048,
                     help="square10: walkers of the tensor-core S vs float64 S comparison")
     return ap.parse_args()
@@ -653,6 +657,176 @@ def run_square16(args):
         dist.destroy_process_group()
 
 
+SYM6 = {"L": 6, "M": 72, "walkers": 4096, "states": 150, "sigma": 0.02, "Wp": 0.9875}
+# sym_hprime_kernel work per (antiparallel bond, hidden unit): cosh(theta - s D)
+# = cosh(theta) cosh(D) - s sinh(theta) sinh(D), two complex multiplies and
+# one complex subtract, then one complex multiply into the running product
+SYM6_FLOP_PER_BOND_UNIT = 20
+
+
+def sym6_oracle_seconds(n_samples=48):
+    """The oracle's B~, HB~, G^(k) and H^(k) for one state at n_samples
+    samples of the sym6 workload (host cores): seconds."""
+    from oracle import rbm, symmetry
+    from paper_2103_08804_gb300 import synth
+    L, M = SYM6["L"], SYM6["M"]
+    N = L * L
+    E0, a = synth.safe_rescaling(L, L)
+    st = [synth.rbm_params(1, N, M, SYM6["sigma"])]
+    psi = synth.rbm_params(2, N, M, SYM6["sigma"])
+    sp = synth.sz0_spins(3, n_samples, N)
+    lref = rbm.logpsi(psi, N, M, sp)
+    t0 = time.perf_counter()
+    Bt = symmetry.b_tilde(st, N, M, L, sp, lref)
+    HBt = symmetry.hb_tilde(st, N, M, L, 1.0, E0, a, SYM6["Wp"], sp, lref)
+    symmetry.gram_by_momentum(Bt)
+    symmetry.gram_by_momentum(Bt, HBt=HBt)
+    return time.perf_counter() - t0
+
+
+def run_sym6(args):
+    """Symmetry projection (Appendix A) on the 6 x 6 lattice: one step =
+    sym_hbtilde for 150 stored states at 4096 samples (4 N = 144 transformed
+    configurations each) and cheb_gram (G and H) for each of the 36 momenta."""
+    import torch
+
+    from paper_2103_08804_gb300 import api, replicas, synth
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    L, M, B, Nm = SYM6["L"], SYM6["M"], SYM6["walkers"], SYM6["states"]
+    N = L * L
+    E0, a = synth.safe_rescaling(L, L)
+    hp = (E0, a, SYM6["Wp"])
+    seed = replicas.replica_seed(11, rank)
+    ctx = api.Context(L, L, M, B, prec=api.FP32)
+    stream = torch.cuda.current_stream()
+    params_h = np.array([synth.rbm_params(seed + n, N, M, SYM6["sigma"]) for n in range(Nm)])
+    psi_h = synth.rbm_params(seed + 1000, N, M, SYM6["sigma"])
+    spins_h = synth.sz0_spins(seed + 2000, B, N)
+    params = torch.tensor(params_h, dtype=torch.complex64, device="cuda")
+    psi = torch.tensor(psi_h, dtype=torch.complex64, device="cuda")
+    spins = torch.tensor(spins_h, device="cuda")
+    lref = ctx.rbm_logpsi(psi, spins)
+    wsbuf = torch.empty(int(ctx.lib.sym_h_workspace_bytes(ctx.h, B)), dtype=torch.uint8,
+                        device="cuda")
+    G = torch.empty(N, Nm, Nm, dtype=torch.complex128, device="cuda")
+    H = torch.empty_like(G)
+
+    def step(p, sp, lr):
+        Bt, HBt = ctx.sym_hbtilde(p, sp, lr, hp, workspace=wsbuf)
+        for k in range(N):
+            ctx.cheb_gram(Bt[k], HBt[k], G[k], H[k])
+
+    K, W = args.steps, max(args.warmup, 3)
+    for _ in range(W):
+        step(params, spins, lref)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_sym6_r{rank}.csv")
+                if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_sym6_r{rank}.csv")
+    launches = 0
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(clk_path, local) as clk:
+        for k in range(K):
+            flush.zero_()
+            l0 = ctx.n_launches()
+            ev[k][0].record(stream)
+            step(params, spins, lref)
+            ev[k][1].record(stream)
+            launches += ctx.n_launches() - l0
+        torch.cuda.synchronize()
+    barrier(ws)
+    ctx.sync_status()
+    ms = max_over_ranks(ws, float(np.mean([e[0].elapsed_time(e[1]) for e in ev])))
+    clocks = clk.summary()
+    moments = Nm * N  # mu_nk = G^(k)_0n for every state and momentum
+    value = ws * moments * 3600.0 * 1000.0 / ms
+
+    # end to end through the public API: stored states, samples and log psi
+    # from pinned host memory, G^(k) and H^(k) back to pinned host memory
+    pin = {"p": torch.from_numpy(params_h.astype(np.complex64)).pin_memory(),
+           "s": torch.from_numpy(spins_h).pin_memory(),
+           "l": lref.cpu().pin_memory()}
+    G_h = torch.empty(G.shape, dtype=G.dtype).pin_memory()
+    H_h = torch.empty_like(G_h).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        p = pin["p"].to("cuda", non_blocking=True)
+        sp = pin["s"].to("cuda", non_blocking=True)
+        lr = pin["l"].to("cuda", non_blocking=True)
+        step(p, sp, lr)
+        G_h.copy_(G, non_blocking=True)
+        H_h.copy_(H, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ws, e0.elapsed_time(e1) / K)
+    Bi = sum(t.numel() * t.element_size() for t in pin.values())
+    Bo = 2 * G_h.numel() * G_h.element_size()
+
+    # live timing of the dominant kernel (sym_hprime_kernel, (H' t_n)(s') /
+    # psi(s) at every transformed configuration), as an FP32 ALU roofline
+    ctx.time_kernel("target", 4096)
+    step(params, spins, lref)
+    torch.cuda.synchronize()
+    kt = ctx.kernel_times()
+    ctx.time_kernel(None, 1)
+    k_ms = float(np.mean(kt)) if kt else None
+    bonds = [(r, (r % L + 1) % L + L * (r // L)) for r in range(N)]
+    bonds += [(r, (r + L) % N) for r in range(N)]
+    anti = sum(int(np.sum(spins_h[:, i] != spins_h[:, j])) for i, j in bonds)
+    flop = 4 * N * anti * M * SYM6_FLOP_PER_BOND_UNIT  # lattice maps keep every bond
+    f_sm = clocks.get("sm_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_sm * 1e6 / 1e12
+    achieved = flop / (k_ms * 1e-3) / 1e12 if k_ms else None
+    roof = {"kernel": "sym_hprime_kernel ((H' t_n)(s') / psi(s) of one state at 4 N B "
+                      "transformed configurations, FP32 FMA over cosh/sinh bond tables)",
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "work_per_launch": flop,
+            "work_note": f"{SYM6_FLOP_PER_BOND_UNIT} flop per (antiparallel bond, hidden unit)",
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
+            "launches_timed": len(kt), "avg_launch_ms": k_ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_s = 48
+        t = sym6_oracle_seconds(n_s)
+        per_step = t * Nm * (B / n_s)
+        cpu = {"value": moments * 3600.0 / per_step, "unit": "moments/hour",
+               "cores": torch.get_num_threads(), "kind": "oracle",
+               "sample": f"one state at {n_s} samples, scaled linearly to {Nm} states x {B} samples"}
+    out = {
+        "metric": "symmetry-projected Chebyshev moments/hour", "value": value,
+        "unit": "moments/hour", "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (f64 local-H' sums and Gram sums)",
+        "data": "synthetic (random complex RBMs, sigma=0.02; seeded S^z=0 samples)",
+        "config": {"workload": f"sym6: periodic 6x6 Heisenberg lattice, alpha=2 (M={M}), "
+                               f"{Nm} stored states, {B} samples, all {N} momenta: B~, HB~ "
+                               "(4N = 144 transformed configurations per sample), G^(k), H^(k)",
+                   "moments_per_step": moments,
+                   "l2": "256 MiB buffer written between timed steps",
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": launches, "clocks": clocks,
+        "e2e": {"value": ws * moments * 3600.0 * 1000.0 / e2e_ms, "unit": "moments/hour",
+                "h2d_bytes_per_step": Bi, "d2h_bytes_per_step": Bo},
+        "roofline": roof, "cpu_baseline": cpu,
+    }
+    del flush, wsbuf
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_explicit(args):
     """Explicit-S workload: one step = one moment with the Cholesky solve."""
     import torch
@@ -963,5 +1137,7 @@ if __name__ == "__main__":
         run_explicit(a)
     elif a.workload == "square16":
         run_square16(a)
+    elif a.workload == "sym6":
+        run_sym6(a)
     else:
         run_ours(a)

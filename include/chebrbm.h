@@ -329,6 +329,27 @@ cr_status sym_btilde(cr_ctx* ctx, const cr_state* states, int Nm, const int8_t* 
                      const void* logpsi_ref, int B, void* workspace, size_t workspace_bytes,
                      void* Bt_out);
 
+/* Appendix A, the projected Hamiltonian H^(k)_nn' = <t~_nk|H'|t~_n'k> /
+   <psi|psi>: sym_btilde plus
+     HB~_nk(s) = <s|H'|t~_nk> / psi(s)
+               = L^-1 sum_m e^{-i 2 pi k.m / L} (1/4) sum_r
+                 (H' t_n)(s'_{m,r}) / psi(s)   (Sec. V bonds),
+   which holds because H' commutes with every translation and rotation of
+   the periodic square lattice.  (H' t_n)(s') is formed from the amplitudes
+   t_n(s'^{ij}) of the exchanged configurations, never as a ratio to
+   t_n(s'), which may vanish: the s' are not samples of |t_n|^2.  hprime: host float64 {E0, a, W'} (a != 0).
+   Bt_out and HBt_out: context precision complex [L*L][Nm][B]; row block k
+   of the two is the (Bmat, HBmat) pair of cheb_gram for momentum k, which
+   then gives G^(k) and H^(k) for cheb_krylov.  workspace: caller-owned
+   device memory of sym_h_workspace_bytes(ctx, B) bytes (sym_workspace_bytes
+   plus theta at the 4 N B transformed configurations, 4 N B M complex
+   values, and two more complex arrays); the call allocates nothing.
+   Errors as sym_btilde; a == 0 or a NULL hprime / HBt_out is CR_EINVAL. */
+size_t sym_h_workspace_bytes(const cr_ctx* ctx, int B);
+cr_status sym_hbtilde(cr_ctx* ctx, const cr_state* states, int Nm, const int8_t* spins,
+                      const void* logpsi_ref, int B, const double* hprime, void* workspace,
+                      size_t workspace_bytes, void* Bt_out, void* HBt_out);
+
 /* Sec. II, Eq. (Aw), with the Jackson damping of Sec. V: the spectral
    function on a frequency grid from the moments mu_n, n = 0 .. Nm - 1,
      A(omega) = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n T_n(omega')]

@@ -30,7 +30,8 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cheb_local_target", "logderiv", "logpsi_backward", "sr_step", "cheb_moment",
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
            "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix",
-           "cheb_spectrum", "cheb_lorentzian", "sym_workspace_bytes", "sym_btilde")
+           "cheb_spectrum", "cheb_lorentzian", "sym_workspace_bytes", "sym_btilde",
+           "sym_h_workspace_bytes", "sym_hbtilde")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
           "chol": 7, "trsv": 8}
 
@@ -103,12 +104,17 @@ def load(path=None):
     lib.sym_workspace_bytes.argtypes = [vp, i]
     lib.sym_workspace_bytes.restype = ctypes.c_size_t
     lib.sym_btilde.argtypes = [vp, ctypes.POINTER(State), i, vp, vp, i, vp, ctypes.c_size_t, vp]
+    lib.sym_h_workspace_bytes.argtypes = [vp, i]
+    lib.sym_h_workspace_bytes.restype = ctypes.c_size_t
+    lib.sym_hbtilde.argtypes = [vp, ctypes.POINTER(State), i, vp, vp, i,
+                                ctypes.POINTER(ctypes.c_double), vp, ctypes.c_size_t, vp, vp]
     lib.cheb_lorentzian.argtypes = [vp, vp, vp, i, d, d, d, vp, i, vp]
     lib.cr_max_chunks.argtypes = [vp]
     lib.logpsi_backward_noalloc.argtypes = [i, i, i, vp, vp, i, vp, vp, vp, ctypes.c_char_p, i]
     for f in SYMBOLS:
         if f not in ("cr_last_error", "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds",
-                     "cr_n_launches", "cr_max_chunks", "sym_workspace_bytes"):
+                     "cr_n_launches", "cr_max_chunks", "sym_workspace_bytes",
+                     "sym_h_workspace_bytes"):
             getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -316,23 +322,43 @@ class Context:
                                         _ptr(S_out)), "sr_smatrix")
         return S_out
 
-    def sym_btilde(self, params, spins, logpsi_ref, workspace=None):
-        """Appendix A: B~_nk(s) for the stored states params [Nm, P] (plain
-        RBMs) at the samples; returns [L*L, Nm, B] (momentum k1 + L k2)."""
+    def _sym_args(self, params, spins, logpsi_ref):
         B = self._spins(spins)
         self._c(logpsi_ref, (B,), "logpsi_ref")
         Nm = params.shape[0]
         if params.dtype != self.cdtype or tuple(params.shape) != (Nm, self.P) \
                 or not params.is_contiguous():
             raise ValueError("params: contiguous [Nm, P] in the context precision")
+        sts = (State * Nm)(*[self.state(params[n]) for n in range(Nm)])
+        return B, Nm, sts
+
+    def sym_btilde(self, params, spins, logpsi_ref, workspace=None):
+        """Appendix A: B~_nk(s) for the stored states params [Nm, P] (plain
+        RBMs) at the samples; returns [L*L, Nm, B] (momentum k1 + L k2)."""
+        B, Nm, sts = self._sym_args(params, spins, logpsi_ref)
         need = int(self.lib.sym_workspace_bytes(self.h, B))
         if workspace is None or workspace.numel() < need:
             workspace = torch.empty(need, dtype=torch.uint8, device=spins.device)
-        sts = (State * Nm)(*[self.state(params[n]) for n in range(Nm)])
         out = torch.empty(self.N, Nm, B, dtype=self.cdtype, device=spins.device)
         self._check(self.lib.sym_btilde(self.h, sts, Nm, _ptr(spins), _ptr(logpsi_ref), B,
                                         _ptr(workspace), need, _ptr(out)), "sym_btilde")
         return out
+
+    def sym_hbtilde(self, params, spins, logpsi_ref, hprime, workspace=None):
+        """Appendix A: (B~_nk(s), HB~_nk(s) = <s|H'|t~_nk> / psi(s)) for the
+        stored states params [Nm, P] at the samples, H' from hprime =
+        (E0, a, W'); each [L*L, Nm, B] (momentum k1 + L k2)."""
+        B, Nm, sts = self._sym_args(params, spins, logpsi_ref)
+        need = int(self.lib.sym_h_workspace_bytes(self.h, B))
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device=spins.device)
+        Bt = torch.empty(self.N, Nm, B, dtype=self.cdtype, device=spins.device)
+        HBt = torch.empty_like(Bt)
+        hp = (ctypes.c_double * 3)(*[float(v) for v in hprime])
+        self._check(self.lib.sym_hbtilde(self.h, sts, Nm, _ptr(spins), _ptr(logpsi_ref), B, hp,
+                                         _ptr(workspace), need, _ptr(Bt), _ptr(HBt)),
+                    "sym_hbtilde")
+        return Bt, HBt
 
     def cheb_spectrum(self, mu, a, Wp, omega, jackson=True):
         """A(omega) of Eq. (Aw) (complex128 [len(omega)]) from the moments mu."""

@@ -1,13 +1,14 @@
 """Symmetry projection (Appendix A) through the C ABI against the oracle:
-B~_nk(s) for every momentum of a 4 x 4 lattice at sampled configurations
-(float64 to 1e-10, float32 to 1e-4 of the largest value), and the
-per-momentum Gram matrices through cheb_gram."""
+B~_nk(s) and HB~_nk(s) = <s|H'|t~_nk> / psi(s) for every momentum of a 4 x 4
+lattice at sampled configurations (float64 to 1e-10, float32 to 1e-4 of the
+largest value), and the per-momentum Gram and Hamiltonian matrices through
+cheb_gram."""
 
 import numpy as np
 import pytest
 
 from gpu_common import dev, host, need_gpu, torch
-from oracle import rbm, symmetry
+from oracle import krylov, rbm, symmetry
 from paper_2103_08804_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -42,6 +43,41 @@ def test_btilde_and_momentum_grams_against_oracle(prec, tol):
     ctx.sync_status()
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-4)])
+def test_hbtilde_and_momentum_hamiltonians_against_oracle(prec, tol):
+    from paper_2103_08804_gb300 import api
+    L, M, B, Nm = 4, 8, 389, 3
+    J, E0, a, Wp = 1.0, -11.2, 9.5, 0.15
+    N = L * L
+    psi = synth.rbm_params(40, N, M, 0.2)
+    states = [synth.rbm_params(41 + n, N, M, 0.2) for n in range(Nm)]
+    spins = synth.sz0_spins(50, B, N)
+    lref = rbm.logpsi(psi, N, M, spins)
+    Bt_ref = symmetry.b_tilde(states, N, M, L, spins, lref)                        # [Nm, N, B]
+    HBt_ref = symmetry.hb_tilde(states, N, M, L, J, E0, a, Wp, spins, lref)
+    # per momentum, the estimators of cheb_gram (sampled H Hermitised)
+    GH_ref = [krylov.gram(Bt_ref[:, k], HBt_ref[:, k]) for k in range(N)]
+    cd = torch.complex128 if prec == 0 else torch.complex64
+    ctx = api.Context(L, L, M, B, prec=prec, J=J)
+    Bt, HBt = ctx.sym_hbtilde(dev(np.array(states), cd), dev(spins, torch.int8), dev(lref, cd),
+                              (E0, a, Wp))
+    for got, ref in ((Bt, Bt_ref), (HBt, HBt_ref)):
+        gh = host(got).astype(np.complex128)                                       # [N, Nm, B]
+        assert np.max(np.abs(gh - np.transpose(ref, (1, 0, 2)))) <= tol * np.abs(ref).max()
+    for k in (0, 1, 5, 10, 15):
+        G = torch.zeros(Nm, Nm, dtype=torch.complex128, device="cuda")
+        H = torch.zeros_like(G)
+        ctx.cheb_gram(Bt[k], HBt[k], G, H)
+        G_ref, H_ref = GH_ref[k]
+        assert np.allclose(host(G), G_ref, rtol=0, atol=10 * tol * np.abs(G_ref).max()), k
+        assert np.allclose(host(H), H_ref, rtol=0, atol=10 * tol * np.abs(H_ref).max()), k
+    # B~ of the H call is the B~ of sym_btilde (to rounding: the rotation
+    # kernel's two variants may contract their arithmetic differently)
+    Bt2 = ctx.sym_btilde(dev(np.array(states), cd), dev(spins, torch.int8), dev(lref, cd))
+    assert float((Bt - Bt2).abs().max()) <= 1e-2 * tol * float(Bt.abs().max())
+    ctx.sync_status()
+
+
 def test_btilde_rejects_chains_and_probe_states():
     from paper_2103_08804_gb300 import api
     ctx = api.Context(8, 1, 4, 16, prec=1)
@@ -49,3 +85,8 @@ def test_btilde_rejects_chains_and_probe_states():
     sp = dev(synth.sz0_spins(1, 16, 8), torch.int8)
     with pytest.raises(api.CRError):
         ctx.sym_btilde(p, sp, torch.zeros(16, dtype=torch.complex64, device="cuda"))
+    sq = api.Context(4, 4, 4, 16, prec=1)
+    p = torch.zeros(1, sq.P, dtype=torch.complex64, device="cuda")
+    sp = dev(synth.sz0_spins(2, 16, 16), torch.int8)
+    with pytest.raises(api.CRError):
+        sq.sym_hbtilde(p, sp, torch.zeros(16, dtype=torch.complex64, device="cuda"), (0.0, 0.0, 0.0))
