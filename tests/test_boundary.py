@@ -64,3 +64,9 @@ def test_null_context_and_bad_arguments_are_rejected(lib_path):
     assert lib.cr_create(ctypes.byref(h), ctypes.byref(odd), 4, 8, 0, 0, None) == 1
     ok = api.Lattice(4, 1, 1.0)
     assert lib.cr_create(ctypes.byref(h), ctypes.byref(ok), 600, 8, 0, 0, None) == 1  # M > 512
+    # the symmetry projection: no context, no workspace size, no call
+    assert lib.sym_workspace_bytes(None, 8) == 0
+    assert lib.sym_h_workspace_bytes(None, 8) == 0
+    assert lib.sym_btilde(None, None, 1, None, None, 8, None, 0, None) == 1
+    hp = (ctypes.c_double * 3)(0.0, 1.0, 0.0)
+    assert lib.sym_hbtilde(None, None, 1, None, None, 8, hp, None, 0, None, None) == 1
