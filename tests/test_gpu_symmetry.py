@@ -78,6 +78,32 @@ def test_hbtilde_and_momentum_hamiltonians_against_oracle(prec, tol):
     ctx.sync_status()
 
 
+def test_hbtilde_at_the_6x6_workload_size_on_sampled_outputs():
+    # the bench's sym6 configuration (6 x 6, M = 72, 4096 samples, float32):
+    # N, M and the bond count exceed a warp, so every strided loop of the
+    # kernels takes several passes; B~ and HB~ of a sample depend on that
+    # sample alone, so the oracle checks 16 of them (the last one included)
+    from paper_2103_08804_gb300 import api
+    L, M, B, Nm, Wp = 6, 72, 4096, 2, 0.9875
+    N = L * L
+    E0, a = synth.safe_rescaling(L, L)
+    psi = synth.rbm_params(60, N, M, 0.02)
+    states = [synth.rbm_params(61 + n, N, M, 0.02) for n in range(Nm)]
+    spins = synth.sz0_spins(70, B, N)
+    lref = rbm.logpsi(psi, N, M, spins)
+    ctx = api.Context(L, L, M, B, prec=api.FP32)
+    Bt, HBt = ctx.sym_hbtilde(dev(np.array(states), torch.complex64), dev(spins, torch.int8),
+                              dev(lref, torch.complex64), (E0, a, Wp))
+    idx = np.append(np.sort(np.random.default_rng(1).choice(B - 1, 15, replace=False)), B - 1)
+    Bt_ref = symmetry.b_tilde(states, N, M, L, spins[idx], lref[idx])
+    HBt_ref = symmetry.hb_tilde(states, N, M, L, 1.0, E0, a, Wp, spins[idx], lref[idx])
+    for got, ref in ((Bt, Bt_ref), (HBt, HBt_ref)):
+        gh = host(got)[:, :, idx].astype(np.complex128)                           # [N, Nm, 16]
+        assert np.all(np.isfinite(gh))
+        assert np.max(np.abs(gh - np.transpose(ref, (1, 0, 2)))) <= 1e-4 * np.abs(ref).max()
+    ctx.sync_status()
+
+
 def test_btilde_rejects_chains_and_probe_states():
     from paper_2103_08804_gb300 import api
     ctx = api.Context(8, 1, 4, 16, prec=1)
