@@ -42,6 +42,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -96,6 +97,13 @@ def barrier(ws):
 def max_over_ranks(ws, x):
     from paper_2103_08804_gb300 import replicas
     return replicas.max_over_ranks(ws, x)
+
+
+def clock_path(name, rank):
+    """Where the nvidia-smi samples of a timed region go: $CHEBRBM_CLOCKS_DIR
+    when set (to keep them), else the system temporary directory."""
+    d = os.environ.get("CHEBRBM_CLOCKS_DIR") or tempfile.gettempdir()
+    return os.path.join(d, f"clocks_{name}_r{rank}.csv")
 
 
 class ClockSampler:
@@ -269,9 +277,7 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD, cyc=CYCLE):
     torch.cuda.synchronize()
     launches0 = ctx.n_launches() + seq.graph_launches
     wall0 = time.perf_counter()
-    clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_{prec_name}_r{rank}.csv")
-                if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                else f"/tmp/clocks_{prec_name}_r{rank}.csv")
+    clk_path = clock_path(prec_name, rank)
     stats = []
     launches = 0  # kernels inside the timed event pairs (restarts excluded)
     with ClockSampler(clk_path, local) as clk:
@@ -726,8 +732,7 @@ def run_sym6(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
-    clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_sym6_r{rank}.csv")
-                if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_sym6_r{rank}.csv")
+    clk_path = clock_path("sym6", rank)
     launches = 0
     barrier(ws)
     torch.cuda.synchronize()
@@ -860,9 +865,7 @@ def run_explicit(args):
     barrier(ws)
     torch.cuda.synchronize()
     launches0 = ctx.n_launches() + seq.graph_launches
-    clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_square10_r{rank}.csv")
-                if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                else f"/tmp/clocks_square10_r{rank}.csv")
+    clk_path = clock_path("square10", rank)
     stats = []
     launches = 0  # kernels inside the timed event pairs (restarts excluded)
     with ClockSampler(clk_path, local) as clk:
@@ -1025,8 +1028,7 @@ def run_batch(args):
     for c in b.ctxs:
         c.sync_status()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    clk_path = (os.path.join(ROOT, "gpurun_out", f"clocks_batch_r{rank}.csv")
-                if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_batch_r{rank}.csv")
+    clk_path = clock_path("batch", rank)
     res = {}
     with ClockSampler(clk_path, local) as clk:
         for schedule in ("batched", "per_q"):
