@@ -1,13 +1,22 @@
 """Symmetry-projected Chebyshev states of the square lattice (Appendix A).
 
 The sequence is computed once for the local probe S^z_00; every momentum
-k = 2 pi (k1, k2) / L follows from translations T_m and 90-degree
-rotations R about site (0, 0):
+k = 2 pi (k1, k2) / L follows from translations T_m and quarter turns R:
     |t~_nk> = L P_k^(T) P^(R) |t_n00>,
     P_k^(T) = L^-2 sum_m e^{-i 2pi k.m / L} T_m,
     P^(R)   = (1 + T_(1,0) R + T_(1,1) R^2 + T_(0,1) R^3) / 4.
 Operators act on basis states by moving spins: (T_m sigma)(x) = sigma(x - m),
-(R sigma)(x) = sigma(R^-1 x) with R (x, y) = (-y, x) mod L.  Then
+(R sigma)(x) = sigma(R^-1 x), so T_m carries the operator S^z_x to S^z_{x+m}
+and R carries it to S^z_{Rx}.
+
+Reading of R: the paper states that P^(R) leaves the exact |t_n00> unchanged
+and that each rotation is followed by the translation that brings the S^z
+operator back to the origin.  Both hold when T_{d_r} R^r fixes the probe
+site, d_r = (0,0), (1,0), (1,1), (0,1), i.e. when R^r takes site (0, 0) to
+-d_r: R is the quarter turn about the plaquette centre (-1/2, -1/2),
+    R (x, y) = (-y - 1, x) mod L,
+and each term T_{d_r} R^r of P^(R) is the r-fold quarter turn about the
+probe site.  Then
     B_{n,m,r}(s) = <s| T_m R^r |t_n00> / <s|psi> = t_n00(s') / psi(s),
     s'(x) = s(R^r x + m),
 and, with the rotation terms of P^(R) folded into the translation sum,
@@ -35,9 +44,10 @@ SHIFTS = ((0, 0), (1, 0), (1, 1), (0, 1))  # translation paired with R^r in P^(R
 
 
 def rotate(x, y, r, L):
-    """R^r (x, y) with R (x, y) = (-y, x) mod L."""
+    """R^r (x, y) with R (x, y) = (-y - 1, x) mod L, the quarter turn about
+    the plaquette centre (-1/2, -1/2)."""
     for _ in range(r % 4):
-        x, y = (-y) % L, x % L
+        x, y = (-y - 1) % L, x % L
     return x, y
 
 

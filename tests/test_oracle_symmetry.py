@@ -7,7 +7,7 @@ symmetric."""
 import numpy as np
 import pytest
 
-from oracle import exact, rbm, symmetry
+from oracle import exact, lattice, rbm, symmetry
 
 
 def _perm_op(basis, L, f):
@@ -126,9 +126,70 @@ def test_momentum_sum_and_symmetric_state():
     assert np.allclose(Bq[0, 1:], 0, atol=1e-12)
 
 
-def test_rotation_is_a_quarter_turn():
+def _turn_about_origin(x, y, L):
+    # quarter turn about site (0, 0), written out independently of the oracle
+    return (L - y) % L, x % L
+
+
+def test_rotation_is_a_quarter_turn_paired_to_fix_the_probe_site():
     L = 5
-    assert symmetry.rotate(1, 0, 1, L) == (0, 1)
-    assert symmetry.rotate(1, 2, 4, L) == (1, 2)
+    for x in range(L):
+        for y in range(L):
+            assert symmetry.rotate(x, y, 4, L) == (x, y)
+    # R^r takes the probe site to -d_r, so T_{d_r} R^r fixes it (Appendix A)
+    for r, (d1, d2) in enumerate(symmetry.SHIFTS):
+        assert symmetry.rotate(0, 0, r, L) == ((-d1) % L, (-d2) % L)
+    # and T_{d_r} R^r is the r-fold quarter turn about the probe site
+    for r, (d1, d2) in enumerate(symmetry.SHIFTS):
+        for x in range(L):
+            for y in range(L):
+                rx, ry = symmetry.rotate(x, y, r, L)
+                qx, qy = x, y
+                for _ in range(r):
+                    qx, qy = _turn_about_origin(qx, qy, L)
+                assert ((rx + d1) % L, (ry + d2) % L) == (qx, qy)
+    # R maps the nearest-neighbour bonds of the periodic lattice onto themselves
+    bonds = {frozenset(b) for b in lattice.bonds(L, L)}
+    site = lambda x, y: x + L * y
+    for i, j in lattice.bonds(L, L):
+        a = symmetry.rotate(i % L, i // L, 1, L)
+        b = symmetry.rotate(j % L, j // L, 1, L)
+        assert frozenset((site(*a), site(*b))) in bonds
     s = np.arange(L * L)[None, :]
     assert np.array_equal(symmetry.transform(symmetry.transform(s, (0, 0), 1, L), (0, 0), 3, L), s)
+
+
+def test_rotation_projector_leaves_a_probe_site_symmetric_state_unchanged():
+    # Appendix A: in the exact calculation P^(R) leaves |t_n00> unchanged.  An
+    # RBM invariant under quarter turns about the probe site (visible biases
+    # symmetric about it, hidden units in orbits of four with the weight
+    # columns turned) must give B~ = the translation projection alone.
+    L, N = 4, 16
+    rng = np.random.default_rng(9)
+    turn = np.array([(lambda q: q[0] + L * q[1])(_turn_about_origin(i % L, i // L, L))
+                     for i in range(N)])                 # site i -> its quarter turn
+    dist = np.array([min(i % L, L - i % L) ** 2 + min(i // L, L - i // L) ** 2
+                     for i in range(N)], dtype=float)
+    a = (0.05 + 0.03j) * dist
+    w = 0.2 * (rng.standard_normal(N) + 1j * rng.standard_normal(N))
+    cols = [w]
+    for _ in range(3):
+        nxt = np.empty(N, dtype=complex)
+        nxt[turn] = cols[-1]                               # weight carried to the turned site
+        cols.append(nxt)
+    M = 4
+    W = np.stack(cols, axis=1)                             # [N, M]
+    b = np.full(M, 0.1 - 0.2j)
+    p = np.concatenate([a, b, W.reshape(-1)])
+    basis = exact.sector_basis(N)[:400]
+    turned = basis[:, np.argsort(turn)]                    # s(turn^-1 x): the turned configuration
+    assert np.allclose(rbm.logpsi(p, N, M, turned), rbm.logpsi(p, N, M, basis))
+    q = rbm.init_params(rng, N, M, 0.2)                    # reference psi, no symmetry needed
+    lref = rbm.logpsi(q, N, M, basis)
+    Bt = symmetry.b_tilde([p], N, M, L, basis, lref)
+    for k1 in range(L):
+        for k2 in range(L):
+            bt = sum(np.exp(-2j * np.pi * (k1 * m1 + k2 * m2) / L)
+                     * np.exp(rbm.logpsi(p, N, M, symmetry.transform(basis, (m1, m2), 0, L)) - lref)
+                     for m1 in range(L) for m2 in range(L)) / L
+            assert np.allclose(Bt[0, k1 + L * k2], bt, atol=1e-12 * np.abs(bt).max() + 1e-14)
