@@ -313,10 +313,12 @@ cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, const void* ta
    (the context's lattice must be square).  For each sample s of |psi|^2 and
    each stored state t_n (plain RBM states, no probe factor):
      B~_nk(s) = L^-1 sum_m e^{-i 2 pi k.m / L} (1/4) sum_{r=0..3}
-                t_n(s'_{m,r}) / psi(s),   s'_{m,r}(x) = s(R^r x + m + d_r),
-   R (x, y) = (-y, x) mod L, d_r = (0,0), (1,0), (1,1), (0,1) (the
-   translation paired with R^r in the rotation projector), i.e. the amplitude
-   ratio of L P_k^(T) P^(R) |t_n>.  states: host array of Nm cr_state;
+                t_n(s'_{m,r}) / psi(s),   s'_{m,r}(x) = s(Q^r x + m),
+   Q (x, y) = (-y, x) mod L the quarter turn about the probe site, i.e. the
+   amplitude ratio of L P_k^(T) P^(R) |t_n>: each term T_{d_r} R^r of the
+   rotation projector (d_r = (0,0), (1,0), (1,1), (0,1), R a quarter turn
+   about a plaquette centre) returns the probe to the origin, so it is Q^r
+   and P^(R) leaves a probe-site-symmetric state unchanged.  states: host array of Nm cr_state;
    spins int8 [B][N]; logpsi_ref: log psi at the samples (context precision
    complex [B]); Bt_out: context precision complex [L*L][Nm][B], momentum
    index k1 + L k2, so that row block k is the Bmat of cheb_gram for that

@@ -1,10 +1,15 @@
 // Symmetry projection of the local Chebyshev sequence onto every momentum
 // of the L x L square lattice (Appendix A).
 //
-// For each sample s, the 4 N transformed configurations
-//   s'(x) = s(R^r x + m + d_r),  r = 0..3, m in the L x L translations,
-//   d_r = (0,0), (1,0), (1,1), (0,1)  (the translation paired with R^r in P^(R)),
-// R (x, y) = (-y, x) mod L, are built once; for each stored state t_n the
+// Each term T_{d_r} R^r of the rotation projector P^(R), d_r = (0,0), (1,0),
+// (1,1), (0,1), is the r-fold quarter turn about the probe site: the paper's
+// R turns the lattice about a plaquette centre and the paired translation
+// returns the S^z operator to the origin, which is what makes P^(R) leave the
+// exact t_n00 unchanged.  So for each sample s the 4 N transformed
+// configurations
+//   s'_{m,r}(x) = s(Q^r x + m),  r = 0..3, m in the L x L translations,
+// with Q (x, y) = (-y, x) mod L the quarter turn about site (0, 0), are built
+// once; for each stored state t_n the
 // log-amplitudes at all of them come from the theta kernel in one launch,
 // then
 //   A_m(s)  = (1/4) sum_r t_n(s'_{m,r}) / psi(s),
@@ -32,7 +37,7 @@ __device__ __forceinline__ void rot(int& x, int& y, int r, int L) {
     }
 }
 
-// out[((r N + m) B + s) N + x] = s(R^r x + m + d_r)
+// out[((r N + m) B + s) N + x] = s(Q^r x + m)
 __global__ void sym_permute_kernel(const int8_t* __restrict__ spins, int B, int L,
                                    int8_t* __restrict__ out) {
     const int N = L * L;
@@ -43,10 +48,9 @@ __global__ void sym_permute_kernel(const int8_t* __restrict__ spins, int B, int 
     const size_t rest = idx / N;
     const int s = (int)(rest % B);
     const int g = (int)(rest / B), r = g / N, m = g % N;
-    const int dx = (r == 1 || r == 2) ? 1 : 0, dy = (r == 2 || r == 3) ? 1 : 0;
     int rx = x % L, ry = x / L;
     rot(rx, ry, r, L);
-    const int src = (rx + m % L + dx) % L + L * ((ry + m / L + dy) % L);
+    const int src = (rx + m % L) % L + L * ((ry + m / L) % L);
     out[idx] = spins[(size_t)s * N + src];
 }
 
