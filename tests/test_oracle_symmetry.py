@@ -193,3 +193,24 @@ def test_rotation_projector_leaves_a_probe_site_symmetric_state_unchanged():
                      * np.exp(rbm.logpsi(p, N, M, symmetry.transform(basis, (m1, m2), 0, L)) - lref)
                      for m1 in range(L) for m2 in range(L)) / L
             assert np.allclose(Bt[0, k1 + L * k2], bt, atol=1e-12 * np.abs(bt).max() + 1e-14)
+
+
+def test_projected_local_probe_is_the_momentum_probe():
+    # For a psi invariant under every lattice map, t_0 = psi with a_0 += i pi/2
+    # is exactly 2i S^z_00 psi, and L P_k^(T) P^(R) S^z_00 psi = S^z_k psi, the
+    # momentum probe of Sec. II, f_k(s) = N^-1/2 sum_r e^{-i k.r} s_r / 2: so
+    # B~_0k(s) = 2i f_k(s) at every momentum (phase convention included).
+    L, M = 4, 3
+    N = L * L
+    psi = np.zeros(rbm.n_params(N, M), dtype=np.complex128)
+    psi[:N] = 0.07 - 0.02j
+    psi[N:N + M] = 0.3 + 0.1j
+    t0 = psi.copy()
+    t0[0] += 0.5j * np.pi
+    spins = exact.sector_basis(N)[::37]
+    lref = rbm.logpsi(psi, N, M, spins)
+    Bt = symmetry.b_tilde([t0], N, M, L, spins, lref)
+    for k1 in range(L):
+        for k2 in range(L):
+            f = lattice.probe(L, L, 2 * np.pi * k1 / L, 2 * np.pi * k2 / L, spins)
+            assert np.allclose(Bt[0, k1 + L * k2], 2j * f, atol=1e-12), (k1, k2)
