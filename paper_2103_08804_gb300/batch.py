@@ -269,7 +269,6 @@ class Batch:
         return out
 
 
-
 def momentum_scan_specs(L=8, alpha=2, chains=(48, 96), walkers=8192, n_moments=150, n_iter=50,
                         sigma=0.02, seed=0, **cfg_kw):
     """Every irreducible momentum of an L x L lattice plus chains of the given
