@@ -44,10 +44,13 @@
  *     H' = (H - E0)/a - W' (Sec. II).
  *   Errors. Argument checks return a status synchronously and set the text
  *     returned by cr_last_error. Failures detected on the device (a
- *     non-positive Cholesky pivot, non-finite estimators or parameters) set a
- *     device status word that cr_sync_status reads and clears. CG that stops
- *     at its iteration limit is not an error: sr_step reports the iteration
- *     count and residual in its stats.
+ *     non-positive Cholesky pivot, non-finite estimators or parameters, a
+ *     bounded device wait that gave up) set a device status word that
+ *     cr_sync_status reads and clears. CG that stops at its iteration limit
+ *     above tolerance is an error (CR_ENOTCONV) only when the caller asks for
+ *     it (cr_sr_opts.cg_strict); sr_step always reports the iteration count
+ *     and residual in its stats, so a fixed CG budget can be run and its
+ *     truncation measured.
  *   B == 0 is valid for every call and launches nothing.
  */
 #ifndef CHEBRBM_H
@@ -167,6 +170,9 @@ typedef struct {
     double cg_tol;          /* CG stops when |r| <= cg_tol |F| */
     int cg_precond;         /* 0: plain CG; 1: Jacobi preconditioner diag(S) + shift */
     int mode;               /* CR_SR_FIT (Sec. III fit) or CR_SR_ENERGY (ground state) */
+    int cg_strict;          /* 1: CG ending at cg_maxit with |r| > cg_tol |F| sets CR_ENOTCONV
+                               in the device status word; 0: it does not (the update
+                               is still applied in both cases) */
 } cr_sr_opts;
 
 /* ---------------------------------------------------------------- context */
@@ -282,20 +288,35 @@ cr_status logpsi_backward(cr_ctx* ctx, const cr_state* state, const int8_t* spin
    N, M and the precision (complex128 for CR_FP64, complex64 otherwise) are
    arguments, and the work runs on `stream` (a cudaStream_t, NULL = legacy
    default stream).  Its reduction scratch is a fixed 4 MiB float64 array in
-   the library's device image (held by every GPU that loads the library until
-   the process exits), which bounds the size: N + M + N*M up to about 131,000
-   parameters (2 <= N <= 1024, 1 <= M <= 512); larger sizes return CR_EINVAL.
-   The call allocates nothing and calls no allocating routine.  The first call
+   the library's device image, which bounds the size: N + M + N*M up to about
+   131,000 parameters (2 <= N <= 1024, 1 <= M <= 512); larger sizes return
+   CR_EINVAL.  The array exists on a device once the CUDA module holding it
+   is loaded there, which the CUDA runtime may do lazily, at the first use of
+   any of that module's symbols on that device (possibly this call's first
+   call); from then on the device holds it until the process exits.  The call
+   itself allocates nothing and calls no allocating routine.  The first call
    on each device looks up the scratch array's device address for that device
-   (cudaGetSymbolAddress), so make that first call before any stream capture.
-   All calls share the one array and it keeps the last call's contents (every
-   entry a call reads is written by that call first, so nothing needs
-   clearing); calls whose work overlaps on the GPU race on it, so serialise
-   them (one stream, or events).  errbuf (host, errbuf_len bytes, or NULL)
-   receives the reason for a non-CR_OK status. */
+   (cudaGetSymbolAddress, which may trigger that module load), so make that
+   first call before any stream capture; doing so also keeps every later call
+   free of driver-side allocation.  Walker sums are accumulated in float32
+   over blocks of 32 walkers and carried in float64, so the result stays as
+   accurate as logpsi_backward's at any walker count.  All calls share the
+   one array and it keeps the last call's contents (every entry a call reads
+   is written by that call first, so nothing needs clearing); calls whose
+   work overlaps on the GPU race on it, so serialise them (one stream, or
+   events).  errbuf (host, errbuf_len bytes, or NULL) receives the reason for
+   a non-CR_OK status. */
 cr_status logpsi_backward_noalloc(int N, int M, cr_prec prec, const int8_t* spins,
                                   const void* tanh_theta, int B, const void* grad_logpsi,
                                   void* grad_params, void* stream, char* errbuf, int errbuf_len);
+
+/* The starting point of projection step n (Sec. III, last paragraph; the
+   paper leaves it open): n == 1: out = psi with a_0 += i pi/2 (exactly
+   2i S^z_0 psi, since e^{i pi sigma/2} = i sigma), so that the first fit starts
+   with weight on H' S^z_q psi; n >= 2: out = prev (RBM_{n-1}, warm start).
+   psi, prev, out: device complex [P] in the context precision (prev ignored
+   for n == 1, psi for n >= 2; out may alias the source). */
+cr_status cheb_init_params(cr_ctx* ctx, int n, const void* psi, const void* prev, void* out);
 
 /* Sec. III natural-gradient update, on samples of |psi|^2:
      gamma = arccos sqrt(min(1, |<R>|^2 / <|R|^2>)),
@@ -304,9 +325,22 @@ cr_status logpsi_backward_noalloc(int N, int M, cr_prec prec, const int8_t* spin
    then solves (S + shift I) dalpha = F in float64 and sets
    params += dalpha. params complex [P] in/out (context precision);
    tanh_theta [B][M] at the samples; R complex [B]; stats_out float64
-   [CR_STATS_LEN] (device) or NULL. */
+   [CR_STATS_LEN] (device) or NULL.  shift >= 0 (shift 0 needs S itself
+   positive definite: a rank-deficient S then gives CR_ESINGULAR on the
+   Cholesky path). */
 cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, const void* tanh_theta,
                   const void* R, int B, const cr_sr_opts* opts, double* stats_out);
+
+/* Sec. III, the matrix-free product of the CG solve on its own:
+     out = (S + shift I) v,  S v = O^dag (O v) / B - <O>^* (<O> . v),
+   computed by the same kernels as the CG of sr_step (in CR_MIXED contexts
+   the O v and O^dag u contractions on the tensor cores, from bf16 splits),
+   with <O> summed over the same samples first.  spins [B][N], tanh_theta
+   [B][M] at the samples; v, out: device complex128 [P]; u_out: context
+   precision complex [B] receiving u = O v (NULL allowed).  For parity
+   checks of the products against an explicit O. */
+cr_status sr_sv(cr_ctx* ctx, const int8_t* spins, const void* tanh_theta, int B, const double* v,
+                double shift, void* u_out, double* out);
 
 /* Appendix A: symmetry projection of one Chebyshev sequence, computed for
    the local probe S^z_00, onto every momentum of the L x L square lattice

@@ -43,12 +43,19 @@ def logpsi(params, N, M, spins):
     return np.asarray(spins, dtype=np.float64) @ a + np.sum(lncosh2(th), axis=-1)
 
 
-def logderiv(params, N, M, spins):
-    """Explicit O_k(s) for each row of spins -> complex [B, P]."""
+def logderiv_from_tanh(spins, T):
+    """Explicit O_k(s) from the spins and T_j(s) = tanh(theta_j(s)):
+    O_a = sigma, O_b = T, O_W = sigma_i T_j -> complex [B, P]."""
     s = np.asarray(spins, dtype=np.float64)
-    T = np.tanh(theta(params, N, M, spins))
+    T = np.asarray(T, dtype=np.complex128)
+    N, M = s.shape[1], T.shape[1]
     OW = (s[:, :, None] * T[:, None, :]).reshape(s.shape[0], N * M)
     return np.concatenate([s.astype(np.complex128), T, OW], axis=1)
+
+
+def logderiv(params, N, M, spins):
+    """Explicit O_k(s) for each row of spins -> complex [B, P]."""
+    return logderiv_from_tanh(spins, np.tanh(theta(params, N, M, spins)))
 
 
 def init_params(rng, N, M, sigma):

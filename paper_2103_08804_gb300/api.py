@@ -31,7 +31,7 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
            "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix",
            "cheb_spectrum", "cheb_lorentzian", "sym_workspace_bytes", "sym_btilde",
-           "sym_h_workspace_bytes", "sym_hbtilde")
+           "sym_h_workspace_bytes", "sym_hbtilde", "cheb_init_params", "sr_sv")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
           "chol": 7, "trsv": 8}
 
@@ -59,7 +59,8 @@ class Target(ctypes.Structure):
 class SROpts(ctypes.Structure):
     _fields_ = [("dgamma", ctypes.c_double), ("shift", ctypes.c_double),
                 ("solver", ctypes.c_int), ("cg_maxit", ctypes.c_int),
-                ("cg_tol", ctypes.c_double), ("cg_precond", ctypes.c_int), ("mode", ctypes.c_int)]
+                ("cg_tol", ctypes.c_double), ("cg_precond", ctypes.c_int), ("mode", ctypes.c_int),
+                ("cg_strict", ctypes.c_int)]
 
 
 _lib = None
@@ -111,6 +112,8 @@ def load(path=None):
     lib.cheb_lorentzian.argtypes = [vp, vp, vp, i, d, d, d, vp, i, vp]
     lib.cr_max_chunks.argtypes = [vp]
     lib.logpsi_backward_noalloc.argtypes = [i, i, i, vp, vp, i, vp, vp, vp, ctypes.c_char_p, i]
+    lib.cheb_init_params.argtypes = [vp, i, vp, vp, vp]
+    lib.sr_sv.argtypes = [vp, vp, vp, i, vp, d, vp, vp]
     for f in SYMBOLS:
         if f not in ("cr_last_error", "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds",
                      "cr_n_launches", "cr_max_chunks", "sym_workspace_bytes",
@@ -296,8 +299,34 @@ class Context:
                                              _ptr(grad_params)), "logpsi_backward")
         return grad_params
 
+    def cheb_init_params(self, n, psi, prev, out):
+        """Starting parameters of projection step n into out (n == 1: psi with
+        a_0 += i pi/2; n >= 2: prev)."""
+        self._c(out, (self.P,), "out")
+        self._c(psi, (self.P,), "psi")
+        self._c(prev, (self.P,), "prev")
+        self._check(self.lib.cheb_init_params(self.h, int(n), _ptr(psi), _ptr(prev), _ptr(out)),
+                    "cheb_init_params")
+        return out
+
+    def sr_sv(self, spins, tanh_theta, v, shift, u_out=None, out=None):
+        """(S + shift I) v through the CG's product kernels (v, out complex128 [P]);
+        u_out (context precision [B]) receives O v."""
+        B = self._spins(spins)
+        self._c(tanh_theta, (B, self.M), "tanh_theta")
+        self._c(u_out, (B,), "u_out")
+        for t, name in ((v, "v"), (out, "out")):
+            if t is not None and not (t.is_cuda and t.dtype == torch.complex128
+                                      and t.is_contiguous() and tuple(t.shape) == (self.P,)):
+                raise ValueError(f"{name}: need a contiguous CUDA complex128 [P] tensor")
+        if out is None:
+            out = torch.empty(self.P, dtype=torch.complex128, device=spins.device)
+        self._check(self.lib.sr_sv(self.h, _ptr(spins), _ptr(tanh_theta), B, _ptr(v), float(shift),
+                                   _ptr(u_out), _ptr(out)), "sr_sv")
+        return out
+
     def sr_step(self, params, spins, tanh_theta, R, dgamma, shift, solver=SOLVE_CG, cg_maxit=100,
-                cg_tol=1e-6, stats_out=None, jacobi=False, mode=0):
+                cg_tol=1e-6, stats_out=None, jacobi=False, mode=0, cg_strict=False):
         B = self._spins(spins)
         self._c(params, (self.P,), "params")
         self._c(tanh_theta, (B, self.M), "tanh_theta")
@@ -305,7 +334,8 @@ class Context:
         if stats_out is not None and not (stats_out.dtype == torch.float64 and stats_out.is_cuda
                                           and stats_out.numel() >= STATS_LEN):
             raise ValueError("stats_out: need a CUDA float64 tensor of 8 entries")
-        o = SROpts(dgamma, shift, solver, cg_maxit, cg_tol, 1 if jacobi else 0, int(mode))
+        o = SROpts(dgamma, shift, solver, cg_maxit, cg_tol, 1 if jacobi else 0, int(mode),
+                   1 if cg_strict else 0)
         self._check(self.lib.sr_step(self.h, _ptr(params), _ptr(spins), _ptr(tanh_theta), _ptr(R),
                                      B, ctypes.byref(o), _ptr(stats_out)), "sr_step")
 

@@ -263,3 +263,36 @@ extern "C" cr_status logderiv(cr_ctx* ctx, const cr_state* st, const int8_t* spi
     CR_CHECK_ARG(spins && theta, "logderiv: null spins or theta");
     return logderiv_impl(ctx, spins, theta, B, tanh_out, O_out);
 }
+
+// ------------------------------------------------- start of projection step n
+//
+// The recursion of Sec. III fits RBM_n from a starting point the paper leaves
+// open.  RBM_1 starts from psi with a_0 += i pi/2: e^{i pi sigma_0 / 2} =
+// i sigma_0, so that RBM equals 2i S^z_0 psi exactly, a state with weight on
+// H' S^z_q psi; RBM_n (n >= 2) starts from RBM_{n-1} (warm start).
+template <typename R>
+__global__ void init_params_kernel(const cpx<R>* __restrict__ src, int P, int shift_a0,
+                                   cpx<R>* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    cpx<R> v = src[k];
+    if (shift_a0 && k == 0) v.y += R(1.5707963267948966);  // + i pi/2
+    out[k] = v;
+}
+
+extern "C" cr_status cheb_init_params(cr_ctx* ctx, int n, const void* psi, const void* prev,
+                                      void* out) {
+    if (!ctx) return CR_EINVAL;
+    CR_CHECK_ARG(n >= 1, "cheb_init_params: n must be >= 1");
+    CR_CHECK_ARG(out && (n == 1 ? psi != nullptr : prev != nullptr),
+                 "cheb_init_params: null parameter vector");
+    const void* src = n == 1 ? psi : prev;
+    const int P = ctx->P, g = (P + 255) / 256;
+    if (ctx->prec == CR_FP64)
+        CR_LAUNCH(ctx, CR_K_OTHER, init_params_kernel<double><<<g, 256, 0, ctx->stream>>>(
+                                       (const cpx<double>*)src, P, n == 1, (cpx<double>*)out));
+    else
+        CR_LAUNCH(ctx, CR_K_OTHER, init_params_kernel<float><<<g, 256, 0, ctx->stream>>>(
+                                       (const cpx<float>*)src, P, n == 1, (cpx<float>*)out));
+    return cr_check_launch(ctx, "init_params_kernel");
+}

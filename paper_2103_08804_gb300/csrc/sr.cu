@@ -28,8 +28,10 @@ cr_status logderiv_impl(cr_ctx* ctx, const int8_t* spins, const void* theta, int
 // writes partial[c][P+2+j] = sum |T_j(s)|^2, the diagonal of <O* O>.  Rows
 // are P + 2 + M long.  Grid (chunk, i-tile): thread t owns hidden units
 // j = t + 128 k and the IT visible units of its tile for O_W; CTAs of tile
-// 0 also produce the a, b and scalar sums.
-template <typename R, int JPT, int IT, bool CONJ>
+// 0 also produce the a, b and scalar sums.  FOLD: the sums run in R over
+// each block of SUB walkers and are then added into float64 accumulators,
+// which bounds the length of every float32 run whatever the chunk length.
+template <typename R, int JPT, int IT, bool CONJ, bool FOLD = false>
 __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__ spins,
                                                       const cpx<R>* __restrict__ T,
                                                       const cpx<R>* __restrict__ g, int B, int N,
@@ -44,15 +46,43 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
     const int s0 = c * chunk, s1 = min(B, s0 + chunk);
     cpx<R> accW[IT][JPT], accb[JPT];
     R acct[JPT];
+    // float64 carries of the FOLD form (unused otherwise)
+    cpx<double> dW[IT][JPT], db[JPT], da = {0.0, 0.0}, dg = {0.0, 0.0};
+    double dt[JPT], dgg = 0.0;
 #pragma unroll
     for (int k = 0; k < JPT; ++k) {
         accb[k] = {R(0), R(0)};
         acct[k] = R(0);
+        db[k] = {0.0, 0.0};
+        dt[k] = 0.0;
 #pragma unroll
-        for (int ii = 0; ii < IT; ++ii) accW[ii][k] = {R(0), R(0)};
+        for (int ii = 0; ii < IT; ++ii) {
+            accW[ii][k] = {R(0), R(0)};
+            dW[ii][k] = {0.0, 0.0};
+        }
     }
     cpx<R> acca = {R(0), R(0)}, accg = {R(0), R(0)};
     R accgg = R(0);
+    // add the float32 block sums into the float64 carries and restart them
+    auto fold = [&]() {
+#pragma unroll
+        for (int k = 0; k < JPT; ++k) {
+            db[k] = db[k] + ccast<double>(accb[k]);
+            dt[k] += (double)acct[k];
+            accb[k] = {R(0), R(0)};
+            acct[k] = R(0);
+#pragma unroll
+            for (int ii = 0; ii < IT; ++ii) {
+                dW[ii][k] = dW[ii][k] + ccast<double>(accW[ii][k]);
+                accW[ii][k] = {R(0), R(0)};
+            }
+        }
+        da = da + ccast<double>(acca);
+        dg = dg + ccast<double>(accg);
+        dgg += (double)accgg;
+        acca = accg = {R(0), R(0)};
+        accgg = R(0);
+    };
     for (int sb = s0; sb < s1; sb += SUB) {
         __syncthreads();
         for (int e = t; e < SUB * IT; e += 128) {
@@ -91,7 +121,9 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
                 accgg += abs2(gq);
             }
         }
+        if (FOLD) fold();
     }
+    if (!FOLD) fold();  // one carry of the whole chunk
     cpx<double>* out = (cpx<double>*)partial + (size_t)c * (P + 2 + M);
 #pragma unroll
     for (int k = 0; k < JPT; ++k) {
@@ -99,18 +131,44 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
         if (j < M) {
 #pragma unroll
             for (int ii = 0; ii < IT; ++ii)
-                if (i0 + ii < N) out[N + M + (size_t)(i0 + ii) * M + j] = ccast<double>(accW[ii][k]);
+                if (i0 + ii < N) out[N + M + (size_t)(i0 + ii) * M + j] = dW[ii][k];
             if (blockIdx.y == 0) {
-                out[N + j] = ccast<double>(accb[k]);
-                if (!CONJ) out[P + 2 + j] = {(double)acct[k], 0.0};
+                out[N + j] = db[k];
+                if (!CONJ) out[P + 2 + j] = {dt[k], 0.0};
             }
         }
     }
-    if (t < IT && i0 + t < N) out[i0 + t] = ccast<double>(acca);
+    if (t < IT && i0 + t < N) out[i0 + t] = da;
     if (blockIdx.y == 0 && t == IT) {
-        out[P] = ccast<double>(accg);
-        out[P + 1] = {(double)accgg, 0.0};
+        out[P] = dg;
+        out[P + 1] = {dgg, 0.0};
     }
+}
+
+// Compensated (Kahan) accumulation: s + c carries the running sum with the
+// low-order part of every addition kept in c (Kahan, CACM 8(1), 1965), so a
+// float32 sum over a walker chunk keeps about twice float32's precision.
+// The float32 walker sums feed F = c (<O* R>/<R> - <O*>) and S = <O* O> -
+// <O*><O>, which cancel when R is nearly constant: plain float32 chunk sums
+// left a relative error of ~1e-5 in the moments of a projection step.
+template <typename R> CR_D void kadd(R& s, R& c, R v) {
+    const R y = v - c;
+    const R t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+template <typename R> CR_D void kadd(cpx<R>& s, cpx<R>& c, cpx<R> v) {
+    kadd(s.x, c.x, v.x);
+    kadd(s.y, c.y, v.y);
+}
+// plain or compensated accumulation, chosen at compile time
+template <bool COMP, typename R> CR_D void acc_add(cpx<R>& s, cpx<R>& c, cpx<R> v) {
+    if constexpr (COMP) kadd(s, c, v);
+    else s = s + v;
+}
+template <bool COMP, typename R> CR_D void acc_add(R& s, R& c, R v) {
+    if constexpr (COMP) kadd(s, c, v);
+    else s += v;
 }
 
 // Register-tiled form of the same reduction (used by the hot path).  Each CTA
@@ -120,8 +178,9 @@ __global__ void __launch_bounds__(128) oreduce_kernel(const int8_t* __restrict__
 // loads.  Y_sj = op(T_sj) g_s is formed once per walker while staging, and
 // the next sub-block's T and spins are fetched into registers while the
 // current one is consumed.  Partial rows and their layout are those of
-// oreduce_kernel.
-template <typename R, bool CONJ>
+// oreduce_kernel.  COMP: Kahan-compensated sums (the estimators of F, Obar
+// and the VJP); plain sums for the CG products of the float32 path.
+template <typename R, bool CONJ, bool COMP = false>
 __global__ void __launch_bounds__(128) oreduce2_kernel(const int8_t* __restrict__ spins,
                                                        const cpx<R>* __restrict__ T,
                                                        const cpx<R>* __restrict__ g, int B, int N,
@@ -140,15 +199,18 @@ __global__ void __launch_bounds__(128) oreduce2_kernel(const int8_t* __restrict_
     const bool a_cta = blockIdx.y == 0, b_cta = blockIdx.z == 0;
     cpx<R> acc[4][4], accb[4];
     R acct[4];
+    // compensation terms (unused, and removed by the compiler, when !COMP)
+    cpx<R> cmp[4][4], cmpb[4];
+    R cmpt[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a][k] = {R(0), R(0)};
-        accb[k] = {R(0), R(0)};
-        acct[k] = R(0);
+        for (int a = 0; a < 4; ++a) acc[a][k] = cmp[a][k] = {R(0), R(0)};
+        accb[k] = cmpb[k] = {R(0), R(0)};
+        acct[k] = cmpt[k] = R(0);
     }
-    cpx<R> acca = {R(0), R(0)}, accg = {R(0), R(0)};
-    R accgg = R(0);
+    cpx<R> acca = {R(0), R(0)}, accg = {R(0), R(0)}, cmpa = {R(0), R(0)}, cmpg = {R(0), R(0)};
+    R accgg = R(0), cmpgg = R(0);
     // register prefetch of one sub-block
     int8_t sp[SE];
     cpx<R> tp[YE];
@@ -198,24 +260,39 @@ __global__ void __launch_bounds__(128) oreduce2_kernel(const int8_t* __restrict_
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    acc[a][k].x = fma(sv[a], y[k].x, acc[a][k].x);
-                    acc[a][k].y = fma(sv[a], y[k].y, acc[a][k].y);
+                    if constexpr (COMP) {
+                        kadd(acc[a][k], cmp[a][k], sv[a] * y[k]);  // sigma = +-1, 0: exact
+                    } else {
+                        acc[a][k].x = fma(sv[a], y[k].x, acc[a][k].x);
+                        acc[a][k].y = fma(sv[a], y[k].y, acc[a][k].y);
+                    }
                 }
             if (ti == 0) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    accb[k] = accb[k] + y[k];
-                    if (!CONJ) acct[k] += abs2(y[k]);
+                    acc_add<COMP>(accb[k], cmpb[k], y[k]);
+                    if (!CONJ) acc_add<COMP>(acct[k], cmpt[k], abs2(y[k]));
                 }
             }
-            if (a_cta && t < TI) acca = acca + sg[q][t] * gs[q];
+            if (a_cta && t < TI) acc_add<COMP>(acca, cmpa, sg[q][t] * gs[q]);
             if (t == 0) {
-                accg = accg + gs[q];
-                accgg += abs2(gs[q]);
+                acc_add<COMP>(accg, cmpg, gs[q]);
+                acc_add<COMP>(accgg, cmpgg, abs2(gs[q]));
             }
         }
     }
-    // partial rows in the context precision (the sums above are in R)
+    // partial rows in the context precision (the sums above are in R); a
+    // compensated sum is s - c (c holds the excess of s)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][k] = acc[a][k] - cmp[a][k];
+        accb[k] = accb[k] - cmpb[k];
+        acct[k] -= cmpt[k];
+    }
+    acca = acca - cmpa;
+    accg = accg - cmpg;
+    accgg -= cmpgg;
     cpx<R>* out = (cpx<R>*)partial + (size_t)c * (P + 2 + M);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -253,18 +330,17 @@ __global__ void combine_kernel(const double* __restrict__ partial, int n_chunks,
     ((cpx<double>*)red)[k] = s;
 }
 
-template <typename R, bool CONJ>
+template <typename R, bool CONJ, bool COMP>
 static cr_status oreduce_t(cr_ctx* c, const int8_t* spins, const void* T, const void* g, int B,
                            double* red_out, const double* skip) {
     const int N = c->N, M = c->M, P = c->P;
     const int nch = c->n_chunks < B ? c->n_chunks : B;
     const int chunk = (B + nch - 1) / nch;
-    const int jpt = (M + 127) / 128;
-    (void)jpt;
     CR_LAUNCH(c, CR_KERNEL_REDUCE,
-              oreduce2_kernel<R, CONJ><<<dim3(nch, (M + 31) / 32, (N + 63) / 64), 128, 0,
-                                         c->stream>>>(spins, (const cpx<R>*)T, (const cpx<R>*)g,
-                                                      B, N, M, P, chunk, c->partial, skip));
+              (oreduce2_kernel<R, CONJ, COMP><<<dim3(nch, (M + 31) / 32, (N + 63) / 64), 128, 0,
+                                                c->stream>>>(spins, (const cpx<R>*)T,
+                                                             (const cpx<R>*)g, B, N, M, P, chunk,
+                                                             c->partial, skip)));
     cr_status s = cr_check_launch(c, "oreduce2_kernel");
     if (s != CR_OK) return s;
     if (!red_out) return CR_OK;  // the caller combines the chunk rows itself
@@ -274,13 +350,18 @@ static cr_status oreduce_t(cr_ctx* c, const int8_t* spins, const void* T, const 
     return cr_check_launch(c, "combine_kernel");
 }
 
+// comp: compensated float32 sums (estimators and the VJP); float64 contexts
+// sum plainly in float64.
 static cr_status oreduce(cr_ctx* c, bool conj_, const int8_t* spins, const void* T, const void* g,
-                         int B, double* red_out, const double* skip) {
+                         int B, double* red_out, const double* skip, bool comp = true) {
     if (c->prec == CR_FP64)
-        return conj_ ? oreduce_t<double, true>(c, spins, T, g, B, red_out, skip)
-                     : oreduce_t<double, false>(c, spins, T, g, B, red_out, skip);
-    return conj_ ? oreduce_t<float, true>(c, spins, T, g, B, red_out, skip)
-                 : oreduce_t<float, false>(c, spins, T, g, B, red_out, skip);
+        return conj_ ? oreduce_t<double, true, false>(c, spins, T, g, B, red_out, skip)
+                     : oreduce_t<double, false, false>(c, spins, T, g, B, red_out, skip);
+    if (comp)
+        return conj_ ? oreduce_t<float, true, true>(c, spins, T, g, B, red_out, skip)
+                     : oreduce_t<float, false, true>(c, spins, T, g, B, red_out, skip);
+    return conj_ ? oreduce_t<float, true, false>(c, spins, T, g, B, red_out, skip)
+                 : oreduce_t<float, false, false>(c, spins, T, g, B, red_out, skip);
 }
 
 // ----------------------------------------------------------------- force
@@ -629,11 +710,13 @@ __global__ void __launch_bounds__(CG_TPB) cg_p_kernel(int P, double tol, double*
     }
 }
 
+// strict: CG that ended at its iteration limit above tolerance (done flag
+// scal[2] unset) reports CR_ENOTCONV in the device status word.
 template <typename R>
 __global__ void apply_update_kernel(cpx<R>* __restrict__ prm, const double* __restrict__ x_, int P,
                                     const double* __restrict__ scal, double* __restrict__ stats,
                                     const double* __restrict__ F_, int* __restrict__ status,
-                                    int cg) {
+                                    int cg, int strict) {
     const cpx<double>* x = (const cpx<double>*)x_;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < P) {
@@ -641,6 +724,7 @@ __global__ void apply_update_kernel(cpx<R>* __restrict__ prm, const double* __re
         if (!isfinite(v.x) || !isfinite(v.y)) set_status(status, CR_ENONFINITE);
         prm[k] = ccast<R>(v);
     }
+    if (k == 0 && strict && scal[2] == 0.0) set_status(status, CR_ENOTCONV);
     if (k == 0 && stats) {
         stats[5] = cg ? scal[3] : 0.0;
         stats[6] = cg ? (scal[1] > 0 ? sqrt(scal[4] / scal[1]) : 0.0) : 0.0;
@@ -721,7 +805,7 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
             } else {
                 s = launch_ov(c, c->p_lo, spins, B, T, c->u_tmp, done);
                 if (s != CR_OK) return s;
-                s = oreduce(c, true, spins, T, c->u_tmp, B, nullptr, done);
+                s = oreduce(c, true, spins, T, c->u_tmp, B, nullptr, done, false);
             }
             if (s != CR_OK) return s;
             CR_LAUNCH(c, CR_KERNEL_CG, cg_apply_kernel<R><<<napp, 256, 0, c->stream>>>(
@@ -736,7 +820,8 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
         }
     }
     CR_LAUNCH(c, CR_K_OTHER, apply_update_kernel<R><<<(P + 255) / 256, 256, 0, c->stream>>>(
-        (cpx<R>*)params, x, P, c->scal, stats, c->F, c->d_status, o->solver == CR_SOLVE_CG || blocked));
+        (cpx<R>*)params, x, P, c->scal, stats, c->F, c->d_status, o->solver == CR_SOLVE_CG || blocked,
+        o->solver == CR_SOLVE_CG && o->cg_strict));
     return cr_check_launch(c, "apply_update");
 }
 
@@ -747,7 +832,7 @@ extern "C" cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, con
     CR_CHECK_ARG(B >= 1 && B <= ctx->max_walkers, "sr_step: B=%d outside [1, %d]", B,
                  ctx->max_walkers);
     CR_CHECK_ARG(spins && tanh_theta && R, "sr_step: null array");
-    CR_CHECK_ARG(opts->shift > 0.0, "sr_step: shift must be > 0");
+    CR_CHECK_ARG(opts->shift >= 0.0, "sr_step: shift must be >= 0");
     CR_CHECK_ARG(opts->solver == CR_SOLVE_CHOLESKY || opts->solver == CR_SOLVE_CG,
                  "sr_step: unknown solver");
     CR_CHECK_ARG(opts->solver != CR_SOLVE_CHOLESKY || (ctx->flags & CR_CTX_EXPLICIT_S),
@@ -756,9 +841,69 @@ extern "C" cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, con
     CR_CHECK_ARG(opts->solver != CR_SOLVE_CG || (opts->cg_maxit >= 1 && opts->cg_tol >= 0.0 &&
                                                  (opts->cg_precond == 0 || opts->cg_precond == 1)),
                  "sr_step: bad CG options");
+    CR_CHECK_ARG(opts->cg_strict == 0 || opts->cg_strict == 1, "sr_step: cg_strict must be 0 or 1");
     return ctx->prec == CR_FP64
                ? sr_step_t<double>(ctx, params, spins, tanh_theta, R, B, opts, stats_out)
                : sr_step_t<float>(ctx, params, spins, tanh_theta, R, B, opts, stats_out);
+}
+
+// v (complex128) into the CG direction p (float64) and its context-precision
+// copy, with the done flag cleared, so that one CG product runs on it.
+template <typename R>
+__global__ void sv_load_kernel(const double* __restrict__ v_, int P, double* __restrict__ cg_,
+                               cpx<R>* __restrict__ p_lo, double* __restrict__ scal) {
+    const cpx<double>* v = (const cpx<double>*)v_;
+    cpx<double>* p = (cpx<double>*)cg_ + 2 * P;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P) {
+        p[k] = v[k];
+        p_lo[k] = ccast<R>(v[k]);
+    }
+    if (k == 0) scal[2] = 0.0;
+}
+
+template <typename R>
+static cr_status sv_t(cr_ctx* c, const int8_t* spins, const void* T, int B, const double* v,
+                      double shift, void* u_out, double* out) {
+    const int P = c->P;
+    double* redO = c->red + 2 * (P + 2 + c->M);
+    cr_status s = oreduce(c, false, spins, T, nullptr, B, redO, nullptr);
+    if (s != CR_OK) return s;
+    CR_LAUNCH(c, CR_K_OTHER, sv_load_kernel<R><<<(P + 255) / 256, 256, 0, c->stream>>>(
+                                 v, P, c->cg, (cpx<R>*)c->p_lo, c->scal));
+    if ((s = cr_check_launch(c, "sv_load")) != CR_OK) return s;
+    const double* done = c->scal + 2;
+    int nch = c->n_chunks < B ? c->n_chunks : B;
+    if (tc_supported(c)) {
+        if ((s = launch_ov_tc(c, c->p_lo, spins, B, T, c->u_tmp, done)) != CR_OK) return s;
+        s = launch_oreduce_tc(c, spins, T, c->u_tmp, B, done, &nch);
+    } else {
+        if ((s = launch_ov(c, c->p_lo, spins, B, T, c->u_tmp, done)) != CR_OK) return s;
+        s = oreduce(c, true, spins, T, c->u_tmp, B, nullptr, done, false);
+    }
+    if (s != CR_OK) return s;
+    const int napp = (P + CGA_K - 1) / CGA_K;
+    CR_LAUNCH(c, CR_KERNEL_CG, cg_apply_kernel<R><<<napp, 256, 0, c->stream>>>(
+                                   c->partial, nch, P + 2 + c->M, redO, P, B, shift, c->cg,
+                                   c->cgpart, c->scal));
+    if ((s = cr_check_launch(c, "cg_apply")) != CR_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(out, c->cg + 6 * (size_t)P, (size_t)P * 16,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && u_out)
+        e = cudaMemcpyAsync(u_out, c->u_tmp, (size_t)B * 2 * sizeof(R), cudaMemcpyDeviceToDevice,
+                            c->stream);
+    return e == cudaSuccess ? CR_OK : cr_fail(c, CR_ECUDA, "sr_sv copy: %s", cudaGetErrorString(e));
+}
+
+extern "C" cr_status sr_sv(cr_ctx* ctx, const int8_t* spins, const void* tanh_theta, int B,
+                           const double* v, double shift, void* u_out, double* out) {
+    if (!ctx) return CR_EINVAL;
+    CR_CHECK_ARG(B >= 1 && B <= ctx->max_walkers, "sr_sv: B=%d outside [1, %d]", B,
+                 ctx->max_walkers);
+    CR_CHECK_ARG(spins && tanh_theta && v && out, "sr_sv: null array");
+    CR_CHECK_ARG(shift >= 0.0, "sr_sv: shift must be >= 0");
+    return ctx->prec == CR_FP64 ? sv_t<double>(ctx, spins, tanh_theta, B, v, shift, u_out, out)
+                                : sv_t<float>(ctx, spins, tanh_theta, B, v, shift, u_out, out);
 }
 
 template <typename R>
@@ -854,7 +999,7 @@ static cudaError_t noalloc_backward_t(int N, int M, const int8_t* spins, const v
     const bool dbl = sizeof(R) == 8;
     double* red = scratch + (size_t)nch * (P + 2 + M) * 2;
 #define LAUNCH(JPT, IT)                                                                    \
-    oreduce_kernel<R, JPT, IT, true><<<dim3(nch, (N + IT - 1) / IT), 128, 0, st>>>(        \
+    oreduce_kernel<R, JPT, IT, true, true><<<dim3(nch, (N + IT - 1) / IT), 128, 0, st>>>(  \
         spins, (const cpx<R>*)T, (const cpx<R>*)g, B, N, M, P, chunk, scratch, nullptr)
     if (jpt == 1) {
         if (dbl) LAUNCH(1, 8); else LAUNCH(1, 16);
@@ -926,6 +1071,9 @@ extern "C" cr_status logpsi_backward_noalloc(int N, int M, cr_prec prec, const i
     }
     if (nch > 64) nch = 64;
     if (nch > B) nch = B;
+    // a launch error still pending from earlier, unrelated work on this thread
+    // is not this call's failure: clear it before the launches below
+    (void)cudaGetLastError();
     e = prec == CR_FP64 ? noalloc_backward_t<double>(N, M, spins, tanh_theta, B, grad_logpsi,
                                                      grad_params, (int)nch, scratch, st)
                         : noalloc_backward_t<float>(N, M, spins, tanh_theta, B, grad_logpsi,

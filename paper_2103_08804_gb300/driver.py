@@ -14,7 +14,7 @@ Order within moment n >= 1 (shared with the oracle):
   mu_n = beta_n < conj(f_q) t~_n / psi > on the fixed samples of |psi|^2,
   together with the Krylov columns B_n and (H' t_n)/psi.
 RBM_1 starts from psi with a_0 += i pi/2 (exactly proportional to
-S^z_0 psi); RBM_n (n >= 2) starts from RBM_{n-1}.
+S^z_0 psi); RBM_n (n >= 2) starts from RBM_{n-1} (cheb_init_params).
 """
 
 from dataclasses import dataclass
@@ -72,11 +72,8 @@ class Sequence:
         self.B = spins_fit.shape[0]
         self.Bref = spins_ref.shape[0]
         psi = np.asarray(psi_params, dtype=np.complex128)
-        init1 = psi.copy()
-        init1[0] += 0.5j * np.pi
         self.params = torch.zeros(Nm, P, dtype=cd, device=dev)
         self.params[0].copy_(torch.from_numpy(psi).to(cd))
-        self.init1 = torch.from_numpy(init1).to(cd).to(dev)
         self.spins = torch.as_tensor(spins_fit, dtype=torch.int8).to(dev).contiguous()
         self.spins_ref = torch.as_tensor(spins_ref, dtype=torch.int8).to(dev).contiguous()
         self.theta = torch.empty(self.B, M, dtype=cd, device=dev)
@@ -168,7 +165,7 @@ class Sequence:
         c, cfg = self.ctx, self.cfg
         replay = iter(replay) if replay is not None else None
         pn = self.params[n]
-        pn.copy_(self.init1 if n == 1 else self.params[n - 1])
+        c.cheb_init_params(n, self.params[0], self.params[n - 1], pn)
         if replay is None:
             c.rbm_logpsi(pn, self.spins, self.theta, self.lp)
             if cfg.n_therm:
@@ -239,7 +236,7 @@ class Sequence:
     def _moment_begin(self, n):
         """Inputs of step n into the fixed buffers, theta and thermalisation."""
         c, cfg = self.ctx, self.cfg
-        self.work.copy_(self.init1 if n == 1 else self.params[n - 1])
+        c.cheb_init_params(n, self.params[0], self.params[n - 1], self.work)
         self.prev_buf.copy_(self.params[n - 1])
         self.beta_buf[0:1].copy_(self.betas[n - 1:n])
         if n >= 2:

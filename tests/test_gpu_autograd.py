@@ -1,7 +1,11 @@
 """The differentiable log psi (torch.autograd.Function over rbm_logpsi /
 logpsi_backward): gradients of a real loss against central finite differences
-on 64 random parameters (real and imaginary directions), and the gradient of
-the overlap loss at alpha_0 against the oracle's analytic force bracket."""
+on 64 random parameters (real and imaginary directions); the same gradient in
+every precision against the oracle's analytic one, sum_s g_s conj(O_k(s))
+with O from oracle.rbm.logderiv (float64 1e-9, float32 1e-5, mixed 1e-3
+relative, the float32 and mixed tolerances of the spec parity bar);
+and the gradient of the overlap loss at alpha_0 against the oracle's analytic
+force bracket in every precision."""
 
 import numpy as np
 import pytest
@@ -78,3 +82,54 @@ def test_overlap_loss_gradient_is_force_bracket():
     bracket = est["OR"] / est["mR"] - np.conj(est["Obar"])
     # PyTorch returns dL/dRe + i dL/dIm = 2 dL/d conj(alpha) = -2 bracket
     assert relerr(host(p.grad), -2.0 * bracket) < 1e-9
+
+
+GRAD_TOL = {0: 1e-9, 1: 1e-5, 2: 1e-3}
+NPDT = {0: np.complex128, 1: np.complex64, 2: np.complex64}
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_gradient_matches_oracle_analytic_gradient(prec):
+    """L = sum_s Re(c_s log psi_s) + |log psi_s|^2 / (2B): PyTorch's gradient is
+    sum_s g_s conj(O_k(s)) with g_s = conj(c_s) + log psi_s / B (twice
+    dL/d conj(log psi_s)), which the oracle forms from its own log psi and O
+    at the same (context-precision) parameters."""
+    from paper_2103_08804_gb300 import api
+    from paper_2103_08804_gb300.autograd import logpsi
+    L, M, B = 64, 128, 4096
+    cd = torch.complex128 if prec == 0 else torch.complex64
+    ctx = api.Context(L, 1, M, B, prec=prec)
+    p0 = synth.rbm_params(11, L, M, 0.05).astype(NPDT[prec]).astype(np.complex128)
+    sp = synth.sz0_spins(12, B, L)
+    c = synth.rbm_params(13, B, 0, 1.0)[:B]
+    p = dev(p0, cd).requires_grad_(True)
+    lp = logpsi(ctx, p, dev(sp, torch.int8))
+    loss = torch.sum((lp * dev(c, cd)).real) + 0.5 * torch.sum(torch.abs(lp) ** 2) / B
+    loss.backward()
+    g = np.conj(c) + rbm.logpsi(p0, L, M, sp) / B
+    want = np.conj(rbm.logderiv(p0, L, M, sp)).T @ g
+    err = relerr(host(p.grad), want)
+    print(f"prec {prec}: gradient against the oracle's analytic gradient {err:.2e}")
+    assert err < GRAD_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_overlap_loss_gradient_is_force_bracket_reduced_precision(prec):
+    from paper_2103_08804_gb300 import api
+    from paper_2103_08804_gb300.autograd import overlap_loss
+    L, M, B = 12, 12, 2048
+    cd = torch.complex64
+    ctx = api.Context(L, 1, M, B, prec=prec)
+    p0n = synth.rbm_params(7, L, M, 0.1).astype(np.complex64).astype(np.complex128)
+    sp = synth.sz0_spins(8, B, L)
+    g = np.random.Generator(np.random.Philox(9))
+    R = (1.0 + 0.2 * (g.standard_normal(B) + 1j * g.standard_normal(B))).astype(np.complex64)
+    p = dev(p0n, cd).requires_grad_(True)
+    spins = dev(sp, torch.int8)
+    lp0 = ctx.rbm_logpsi(dev(p0n, cd), spins)
+    overlap_loss(ctx, p, spins, lp0, dev(R, cd)).backward()
+    est = sr.estimators(rbm.logderiv(p0n, L, M, sp), R.astype(np.complex128))
+    bracket = est["OR"] / est["mR"] - np.conj(est["Obar"])
+    err = relerr(host(p.grad), -2.0 * bracket)
+    print(f"prec {prec}: overlap-loss gradient against the force bracket {err:.2e}")
+    assert err < GRAD_TOL[prec]

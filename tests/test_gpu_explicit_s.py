@@ -5,7 +5,10 @@ order only); float32 contexts form float32 products (relative ~1e-7); mixed
 contexts form it on the tensor cores from bf16 splits of both operands with
 float32 accumulation: three-term splits (six products, float32-like, held
 to 2e-6 relative in the Frobenius norm) by default, two-term splits (three
-products, ~2^-16 relative per product, held to 1e-4) with CR_CTX_S_BF16X3.
+products, ~2^-16 relative per product, held to 1e-4) with CR_CTX_S_BF16X3;
+and element by element (the largest entry error against the largest entry,
+so that one bad tile or row fails) against the oracle's S of the same
+rounded inputs.
 
 Solve: the blocked Cholesky plus float64 refinement must certify, by its
 own float64 residual, that it solved the system the GPU built
@@ -27,6 +30,12 @@ pytestmark = pytest.mark.gpu
 PREC = {"fp64": (0, torch.complex128), "fp32": (1, torch.complex64),
         "mixed": (2, torch.complex64), "mixed_x3": (2, torch.complex64)}
 S_TOL = {"fp64": 1e-12, "fp32": 1e-6, "mixed": 2e-6, "mixed_x3": 1e-4}
+# Element by element, max_kl |S_kl - S_kl^ref| / max |S^ref|, against the
+# oracle's S built from the same (context-precision) tanh(theta) values, so
+# that only the arithmetic of the build is measured: float32 products summed
+# in float64 (~1e-7), tensor-core products summed in float32 per walker
+# chunk (~1e-6), two-term splits (~2^-16 per product).
+S_EL_TOL = {"fp64": 1e-12, "fp32": 1e-6, "mixed": 4e-6, "mixed_x3": 2e-4}
 # (Lx, Ly, M, walkers): P = 560 (chain), 424 (4 x 4 square), 2144 (chain)
 SHAPES = [(16, 1, 32, 2000), (4, 4, 24, 777), (32, 1, 64, 4096)]
 
@@ -68,6 +77,12 @@ def test_explicit_s_against_oracle(prec, shape):
     ctx.sync_status()
     err = np.linalg.norm(S - S_ref) / np.linalg.norm(S_ref)
     assert err < S_TOL[prec], err
+    T_in = O[:, N:N + M].astype(np.complex64 if cd == torch.complex64 else np.complex128)
+    S_in = sr.qgt(sr.estimators(rbm.logderiv_from_tanh(spins, T_in), R)) + shift * np.eye(O.shape[1])
+    el = np.max(np.abs(S - S_in)) / np.max(np.abs(S_in))
+    worst = np.unravel_index(np.argmax(np.abs(S - S_in)), S.shape)
+    print(f"{prec} {shape}: S Frobenius {err:.2e}, element-wise {el:.2e} at {worst}")
+    assert el < S_EL_TOL[prec], (el, worst)
     A = S - S.conj().T
     np.fill_diagonal(A, 0)
     assert not A.any()                            # off-diagonal mirrored exactly

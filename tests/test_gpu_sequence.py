@@ -16,7 +16,9 @@ Three gates:
     backward-stable solve, 2 P u kappa(S + lambda I) |dalpha| (u = 2^-53);
   * replay: the CUDA path consumes the walker configurations the oracle
     recorded (no sampling on either side), so all differences are arithmetic:
-    float64 within 1e-6 mu_0, float32 within the 1e-3 moment-error bound.
+    one projection step from the oracle's inputs within 1e-9 mu_0 (float64),
+    1e-5 mu_0 (float32) and 1e-3 mu_0 (mixed); the whole float64 recursion
+    within 1e-6 mu_0.
 """
 
 import numpy as np
@@ -105,7 +107,7 @@ def test_fp64_lockstep_every_iteration(e0):
     worst = 0.0
     for n in range(1, WL.moments):
         pn = seq.params[n]
-        pn.copy_(seq.init1 if n == 1 else seq.params[n - 1])
+        ctx.cheb_init_params(n, seq.params[0], seq.params[n - 1], pn)
         ctx.rbm_logpsi(pn, seq.spins, seq.theta, seq.lp)
         ctx.mc_sweep(pn, seq.spins, seq.theta, cfg.n_therm, seq.rng, logpsi_out=seq.lp,
                      tanh_out=seq.tanh)
@@ -167,19 +169,19 @@ def _oracle_single_step(ref, e0, n, solver):
     beta = np.mean(R_at(params, ref.samples[n][WL.iters]))
     lp_ref = rbm.logpsi(psi, N, M, ref.spins_ref)
     f = lattice.probe(12, 1, WL.q[0], WL.q[1], ref.spins_ref)
-    mu = beta * np.mean(np.conj(f) * target.rel_amplitude(State(params), N, M, 12, 1, WL.q,
-                                                          ref.spins_ref, lp_ref))
-    return params, beta, mu
+    Bn = beta * target.rel_amplitude(State(params), N, M, 12, 1, WL.q, ref.spins_ref, lp_ref)
+    return params, beta, np.mean(np.conj(f) * Bn), Bn
 
 
 def _single_steps(seq, ref, e0, solver):
     """Each projection step n alone: the GPU takes the oracle's t~_{n-1},
     t~_{n-2}, beta_{n-1}, beta_{n-2} and recorded samples, fits t~_n and
     measures beta_n, mu_n; the oracle does the same with the same solver.
-    Returns per-n relative errors of (mu_n, beta_n, parameters of t~_n)."""
+    Returns per-n relative errors of (mu_n, beta_n, parameters of t~_n, the
+    state beta_n t~_n / psi on the reference samples in the mean-square norm)."""
     cd = seq.ctx.cdtype
     seq.start(replay_ref=dev(ref.spins_ref, torch.int8))
-    e_mu, e_beta, e_par = [], [], []
+    e_mu, e_beta, e_par, e_B = [], [], [], []
     mu0 = abs(ref.mu[0])
     for n in range(1, seq.cfg.n_moments):
         for k in range(max(1, n - 2), n):
@@ -187,11 +189,12 @@ def _single_steps(seq, ref, e0, solver):
         seq.betas[:n].copy_(dev(np.array(ref.betas[:n]), torch.complex128))
         seq.fit(n, replay=[dev(s, torch.int8) for s in ref.samples[n]])
         seq.ctx.sync_status()
-        p, beta, mu = _oracle_single_step(ref, e0, n, solver)
+        p, beta, mu, Bn = _oracle_single_step(ref, e0, n, solver)
         e_mu.append(abs(host(seq.mu)[n] - mu) / mu0)
         e_beta.append(abs(host(seq.betas)[n] - beta) / abs(beta))
         e_par.append(np.max(np.abs(host(seq.params[n]) - p)) / np.max(np.abs(p)))
-    return np.array(e_mu), np.array(e_beta), np.array(e_par)
+        e_B.append(np.sqrt(np.mean(np.abs(host(seq.Bmat)[n] - Bn) ** 2) / np.mean(np.abs(Bn) ** 2)))
+    return np.array(e_mu), np.array(e_beta), np.array(e_par), np.array(e_B)
 
 
 # One projection step from the oracle's inputs.  float64 paths: each side
@@ -200,34 +203,43 @@ def _single_steps(seq, ref, e0, solver):
 # difference e in the inputs of a solve reaches kappa e in dalpha:
 #   Cholesky: rounding only, agreement to 1e-9;
 #   CG: two solves stopping at |r| <= 1e-10 |F| may differ by kappa 1e-10.
-# float32 paths, against the oracle's direct solve: products with
-# u = 6e-8 leave ~kappa u in each update (parameters to 1e-2), while the
-# moment, an average over |psi|^2, stays far more accurate.
-# Tolerances (mu / mu_0, beta relative, parameters relative), ~10x the measured.
+# float32 and mixed paths, against the oracle's direct solve: the moments are
+# held to the parity bar of the benchmark spec, 1e-5 mu_0 (float32) and 1e-3 mu_0
+# (mixed), with the walker sums of F and <O> compensated (float32 chunk sums
+# left ~1e-5); the float32 CG runs to 1e-7.  beta_n and the parameters are
+# not invariant under the near-null directions of S + lambda I (a scale of
+# t~_n moves beta_n against it, kappa amplifies both), so the state itself,
+# beta_n t~_n / psi on the reference samples (the Krylov column B_n), is
+# gated in the mean-square norm at the moment tolerance, and beta_n and the
+# parameters at 10x their measured errors.
+# Tolerances: (mu / mu_0, beta relative, parameters relative, B_n rms relative).
 SOLVERS = {"cholesky": dict(solver="cholesky"),
            "cg": dict(solver="cg", cg_maxit=400, cg_tol=1e-10, jacobi=False),
            "pcg": dict(solver="cg", cg_maxit=400, cg_tol=1e-10, jacobi=True)}
+CG_TOL = {"fp64": 1e-10, "fp32": 1e-7, "mixed": 1e-5}
 
 
-@pytest.mark.parametrize("path,tol", [("fp64-cholesky", (1e-9, 1e-9, 1e-9)),
-                                      ("fp64-cg", (1e-5, 1e-3, 1e-3)),
-                                      ("fp64-pcg", (1e-4, 1e-2, 1e-2)),
-                                      ("fp32-cholesky", (2e-4, 0.1, 2e-2)),
-                                      ("fp32-pcg", (4e-3, 0.5, 0.2)),
-                                      ("mixed-pcg", (4e-3, 0.5, 0.2))])
+@pytest.mark.parametrize("path,tol", [("fp64-cholesky", (1e-9, 1e-9, 1e-9, 1e-9)),
+                                      ("fp64-cg", (1e-5, 1e-3, 1e-3, 1e-5)),
+                                      ("fp64-pcg", (1e-4, 1e-2, 1e-2, 1e-4)),
+                                      ("fp32-cholesky", (1e-5, 1e-2, 1e-2, 1e-5)),
+                                      ("fp32-pcg", (1e-5, 1e-2, 1e-2, 1e-5)),
+                                      ("mixed-cg", (1e-3, 0.5, 0.2, 1e-3)),
+                                      ("mixed-pcg", (1e-3, 0.5, 0.2, 1e-3))])
 def test_single_projection_step_replay(e0, recorded, path, tol):
     from paper_2103_08804_gb300 import api
     prec_s, sol = path.split("-")
     prec = {"fp64": api.FP64, "fp32": api.FP32, "mixed": api.MIXED}[prec_s]
     solver = api.SOLVE_CHOLESKY if sol == "cholesky" else api.SOLVE_CG
-    cg_tol = 1e-10 if prec == api.FP64 else 1e-5
-    seq, _ = _seq(prec, e0, WL.moments, solver, cg_tol=cg_tol, cg_maxit=400,
+    seq, _ = _seq(prec, e0, WL.moments, solver, cg_tol=CG_TOL[prec_s], cg_maxit=1000,
                   jacobi=(sol == "pcg"))
     ref_solver = SOLVERS[sol] if prec == api.FP64 else SOLVERS["cholesky"]
-    e_mu, e_beta, e_par = _single_steps(seq, recorded, e0, ref_solver)
+    e_mu, e_beta, e_par, e_B = _single_steps(seq, recorded, e0, ref_solver)
     print(f"{path} single-step errors: mu {e_mu.max():.2e} beta {e_beta.max():.2e} "
-          f"params {e_par.max():.2e}")
+          f"params {e_par.max():.2e} state {e_B.max():.2e}; per-n mu "
+          + np.array2string(e_mu, precision=1))
     assert e_mu.max() < tol[0] and e_beta.max() < tol[1] and e_par.max() < tol[2]
+    assert e_B.max() < tol[3]
 
 
 def test_fp64_replay_accumulated_over_sequence(e0, recorded):
@@ -245,12 +257,15 @@ def test_fp64_replay_accumulated_over_sequence(e0, recorded):
 
 
 def test_fp32_replay_accumulated_over_sequence_reported(e0, recorded):
-    """Accumulated float32 moment error on the recorded samples, per n (report;
-    the gate is that the first steps meet the float32 single-step bound)."""
+    """Accumulated float32 moment error on the recorded samples, per n.  Every
+    step's error feeds the later targets and the recursion amplifies it (the
+    float64 replay above measures about x10 per moment late in this
+    sequence), so the parity gate is the single-step bound on the first step
+    (1e-5 mu_0) and the later moments are reported."""
     from paper_2103_08804_gb300 import api
     seq, _ = _seq(api.FP32, e0, WL.moments, api.SOLVE_CHOLESKY)
     mu, _ = _replay(seq, recorded)
     err = np.abs(mu - np.array(recorded.mu)) / abs(recorded.mu[0])
     print("fp32 accumulated replay moment error per n:", np.array2string(err, precision=2))
-    assert err[0] < 1e-6 and err[1] < 1e-4
+    assert err[0] < 1e-6 and err[1] < 1e-5
     assert np.all(np.isfinite(mu))

@@ -104,8 +104,7 @@ def test_natural_gradient_fit_converges_on_representable_target():
     rng = np.random.default_rng(13)
     p0 = rbm.init_params(rng, N, M, 0.3)
     phi = 1j * basis[:, 0] * _dense_psi(p0, N, M, basis)
-    p = p0.copy()
-    p[0] += 0.5j * np.pi
+    p = chebyshev.initial_params(p0, None, 1)
     p = p + 0.02 * (rng.standard_normal(len(p)) + 1j * rng.standard_normal(len(p)))
     gammas = []
     for _ in range(40):
@@ -114,6 +113,24 @@ def test_natural_gradient_fit_converges_on_representable_target():
         p, info = sr.sr_step(p, rbm.logderiv(p, N, M, basis), phi / psi, 1e-6, 0.5, weights=w / w.sum())
         gammas.append(info["gamma"])
     assert gammas[-1] < 1e-3 * gammas[0]
+
+
+def test_initial_params_start_from_the_probe_site_operator():
+    """The start of projection step 1 (Sec. III leaves it open): the RBM with
+    a_0 += i pi/2 is exactly i sigma_0 psi = 2i S^z_0 psi on every
+    configuration (e^{i pi sigma/2} = i sigma); step n >= 2 starts from a copy
+    of RBM_{n-1}."""
+    N, M = 8, 6
+    basis = exact.sector_basis(N)
+    rng = np.random.default_rng(14)
+    psi = rbm.init_params(rng, N, M, 0.3)
+    prev = rbm.init_params(rng, N, M, 0.3)
+    p1 = chebyshev.initial_params(psi, prev, 1)
+    ratio = _dense_psi(p1, N, M, basis) / _dense_psi(psi, N, M, basis)
+    assert np.allclose(ratio, 1j * basis[:, 0], atol=1e-13)
+    p3 = chebyshev.initial_params(psi, prev, 3)
+    assert np.array_equal(p3, prev) and p3 is not prev
+    assert np.array_equal(chebyshev.initial_params(psi, prev, 2), prev)
 
 
 def _cfg(**kw):

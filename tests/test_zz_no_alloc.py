@@ -2,7 +2,9 @@
 allocate device memory (its reduction scratch is a fixed array inside the
 library).  Checked through the C ABI against logpsi_backward on two calls in
 a row with different inputs, within the kernel-parity tolerances (float64
-1e-10, float32 1e-4 relative), plus the size limit.  Collected last so that a
+1e-10, float32 1e-4 relative), at the 16 x 16 lattice size near the scratch
+limit (66,048 parameters, 65536 walkers in two chunks, float32 within 1e-5),
+plus the size limit.  Collected last so that a
 stop at the first failure has run every other test."""
 
 import ctypes
@@ -54,6 +56,38 @@ def test_noalloc_backward_matches_context_backward_twice(prec, tol, shape):
                                         ctypes.c_void_p(stream.cuda_stream), err, len(err))
         assert s == 0, err.value
         assert relerr(host(got), host(want)) < tol, call
+
+
+def test_noalloc_backward_near_its_size_limit():
+    """N = M = 256: the scratch holds two partial rows, so each chunk sums
+    32768 walkers; its float32 runs stay 32 walkers long (float64 carries)."""
+    from paper_2103_08804_gb300 import api
+    Lx = Ly = 16
+    N, M, B = 256, 256, 65536
+    lib = api.load()
+    ctx = api.Context(Lx, Ly, M, B, prec=1)
+    stream = torch.cuda.current_stream()
+    err = ctypes.create_string_buffer(256)
+    cd = torch.complex64
+    params, spins, g = _inputs(300, N, M, B, cd)
+    params = synth.rbm_params(300, N, M, 0.01)
+    th = torch.empty(B, M, dtype=cd, device="cuda")
+    T = torch.empty(B, M, dtype=cd, device="cuda")
+    ctx.rbm_logpsi(dev(params, cd), spins, theta_out=th)
+    ctx.logderiv(dev(params, cd), spins, th, tanh_out=T)
+    del th
+    want = ctx.logpsi_backward(dev(params, cd), spins, T, g)
+    for call in range(2):
+        got = torch.full((ctx.P,), float("nan"), dtype=cd, device="cuda")
+        s = lib.logpsi_backward_noalloc(N, M, 1, ctypes.c_void_p(spins.data_ptr()),
+                                        ctypes.c_void_p(T.data_ptr()), B,
+                                        ctypes.c_void_p(g.data_ptr()),
+                                        ctypes.c_void_p(got.data_ptr()),
+                                        ctypes.c_void_p(stream.cuda_stream), err, len(err))
+        assert s == 0, err.value
+        e = relerr(host(got), host(want))
+        print(f"noalloc at N = M = 256, B = 65536: {e:.2e}")
+        assert e < 1e-5, call
 
 
 def test_noalloc_backward_rejects_sizes_beyond_its_scratch():
