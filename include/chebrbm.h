@@ -216,6 +216,7 @@ cr_status cr_sync_status(cr_ctx* ctx);
 #define CR_KERNEL_SBUILD 6  /* explicit S: Gram matrix of O */
 #define CR_KERNEL_CHOL 7    /* blocked Cholesky factor (potrf, trsm, syrk) */
 #define CR_KERNEL_TRSV 8    /* triangular solves of the refinement */
+#define CR_KERNEL_FCG 9     /* fused CG solve (mixed contexts: one launch per solve) */
 long long cr_n_launches(const cr_ctx* ctx);
 cr_status cr_time_kernel(cr_ctx* ctx, int kernel_id, int capacity);
 int cr_kernel_times(cr_ctx* ctx, float* ms_out, int capacity);

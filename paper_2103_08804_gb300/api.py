@@ -33,7 +33,7 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cheb_spectrum", "cheb_lorentzian", "sym_workspace_bytes", "sym_btilde",
            "sym_h_workspace_bytes", "sym_hbtilde", "cheb_init_params", "sr_sv")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
-          "chol": 7, "trsv": 8}
+          "chol": 7, "trsv": 8, "fcg": 9}
 
 
 class Lattice(ctypes.Structure):

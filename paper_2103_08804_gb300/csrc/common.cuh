@@ -196,6 +196,16 @@ struct cr_ctx {
     int n_gtiles;
     long long n_launches;    // kernels launched so far
     cr_ktimer kt;
+    // fused CG solve (cg_fused.cu; mixed contexts with N, M <= 256)
+    int fcg;                 // 1 when the fused solve covers this context
+    unsigned char* fcg_a1;   // sigma operand tiles of the O v contraction
+    unsigned char* fcg_b2;   // sigma^T operand chunks of the O^dag w contraction
+    unsigned char* fcg_v2;   // bf16 planes of the W part of p
+    size_t fcg_v2plane;
+    void* fcg_vab;           // float32 a- and b-parts of p [N + M]
+    void* fcg_part;          // partial rows, complex float32 [n_sm][P]
+    double* fcg_psc;         // scalar partials [n_sm][8]
+    unsigned* fcg_bar;       // grid-barrier counter and abort flag
 };
 
 static inline int rsize(const cr_ctx* c) { return c->prec == CR_FP64 ? 8 : 4; }
@@ -228,6 +238,14 @@ cr_status chol_refine_solve(cr_ctx* c, const double* F, int maxit);
 cr_status launch_sbuild_tc(cr_ctx* c, const int8_t* spins, const void* T, int B,
                            const double* redO, double shift);
 void launch_smirror(cr_ctx* c);  // S[k][l] = conj(S[l][k]) for k < l
+
+// Fused CG solve (cg_fused.cu).
+bool fcg_supported(const cr_ctx* c);
+void fcg_sizes(const cr_ctx* c, size_t* a1, size_t* b2, size_t* v2plane, size_t* part);
+cr_status fcg_prepare(cr_ctx* c);
+cr_status launch_cg_fused(cr_ctx* c, const int8_t* spins, const void* T, int B, const double* redO,
+                          double shift, double tol, int maxit, int precond, int apply_only,
+                          const double* v_in, void* u_out);
 
 // Tables for a state (rbm.cu).
 cr_status build_tables(cr_ctx* c, const void* params, int slot);

@@ -177,22 +177,37 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
         }
         if (chol_blocked(c)) ALLOC(c->Lf, chol_factor_bytes(c));
     }
+    int dev = 0;
+    c->n_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    c->fcg = e == cudaSuccess && fcg_supported(c) ? 1 : 0;
+    if (c->fcg) {
+        size_t a1, b2, v2p, part;
+        fcg_sizes(c, &a1, &b2, &v2p, &part);
+        c->fcg_v2plane = v2p;
+        ALLOC(c->fcg_a1, a1);
+        ALLOC(c->fcg_b2, b2);
+        ALLOC(c->fcg_v2, 3 * v2p);
+        ALLOC(c->fcg_vab, (size_t)(c->N + M) * 8);
+        ALLOC(c->fcg_part, part);
+        ALLOC(c->fcg_psc, (size_t)c->n_sm * 8 * sizeof(double));
+        ALLOC(c->fcg_bar, 4 * sizeof(unsigned));
+        // padding entries of the V planes (sites past N, columns past 2M) stay zero
+        if (e == cudaSuccess) e = cudaMemset(c->fcg_v2, 0, 3 * v2p);
+    }
 #undef ALLOC
     if (e != cudaSuccess) {
         cr_destroy(c);
         return e == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;
     }
-    int dev = 0;
-    c->n_sm = 1;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
     std::vector<int2> bonds = make_bonds(c->Lx, c->Ly);
     e = cudaMemcpy(c->d_bonds, bonds.data(), Nb * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !gt.empty())
         e = cudaMemcpy(c->gtiles, gt.data(), gt.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, 64 * sizeof(double));
-    if (e != cudaSuccess || tc_prepare(c) != CR_OK) {
+    if (e != cudaSuccess || tc_prepare(c) != CR_OK || (c->fcg && fcg_prepare(c) != CR_OK)) {
         cr_destroy(c);
         return CR_ECUDA;
     }
@@ -205,7 +220,8 @@ extern "C" cr_status cr_destroy(cr_ctx* c) {
     kt_free(c);
     void* ptrs[] = {c->d_status, c->d_bonds, c->theta_tmp, c->lp_tmp, c->u_tmp, c->partial,
                     c->red, c->F, c->cg, c->p_lo, c->cgpart, c->scal, c->S, c->O_tmp, c->kry,
-                    c->Lf, c->Xt, c->gtiles};
+                    c->Lf, c->Xt, c->gtiles, c->fcg_a1, c->fcg_b2, c->fcg_v2, c->fcg_vab,
+                    c->fcg_part, c->fcg_psc, c->fcg_bar};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int s = 0; s < 2; ++s) {

@@ -787,6 +787,11 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
             CR_LAUNCH(c, CR_K_OTHER, fnorm_kernel<<<1, 1024, 0, c->stream>>>(c->F, P, c->scal));
             if ((s = cr_check_launch(c, "cholesky path")) != CR_OK) return s;
         }
+    } else if (c->fcg) {
+        // mixed precision: the whole CG in one persistent tensor-core kernel
+        s = launch_cg_fused(c, spins, T, B, redO, o->shift, o->cg_tol, o->cg_maxit, o->cg_precond,
+                            0, nullptr, nullptr);
+        if (s != CR_OK) return s;
     } else {
         CR_LAUNCH(c, CR_K_OTHER, cg_init_kernel<R><<<1, 1024, 0, c->stream>>>(
                                      c->F, redO, c->N, c->M, P, B, o->shift, o->cg_precond,
@@ -869,6 +874,13 @@ static cr_status sv_t(cr_ctx* c, const int8_t* spins, const void* T, int B, cons
     double* redO = c->red + 2 * (P + 2 + c->M);
     cr_status s = oreduce(c, false, spins, T, nullptr, B, redO, nullptr);
     if (s != CR_OK) return s;
+    if (c->fcg) {
+        s = launch_cg_fused(c, spins, T, B, redO, shift, 0.0, 1, 0, 1, v, u_out);
+        if (s != CR_OK) return s;
+        cudaError_t e = cudaMemcpyAsync(out, c->cg + 6 * (size_t)P, (size_t)P * 16,
+                                        cudaMemcpyDeviceToDevice, c->stream);
+        return e == cudaSuccess ? CR_OK : cr_fail(c, CR_ECUDA, "sr_sv copy: %s", cudaGetErrorString(e));
+    }
     CR_LAUNCH(c, CR_K_OTHER, sv_load_kernel<R><<<(P + 255) / 256, 256, 0, c->stream>>>(
                                  v, P, c->cg, (cpx<R>*)c->p_lo, c->scal));
     if ((s = cr_check_launch(c, "sv_load")) != CR_OK) return s;

@@ -208,10 +208,14 @@ def _single_steps(seq, ref, e0, solver):
 # (mixed), with the walker sums of F and <O> compensated (float32 chunk sums
 # left ~1e-5); the float32 CG runs to 1e-7.  beta_n and the parameters are
 # not invariant under the near-null directions of S + lambda I (a scale of
-# t~_n moves beta_n against it, kappa amplifies both), so the state itself,
-# beta_n t~_n / psi on the reference samples (the Krylov column B_n), is
-# gated in the mean-square norm at the moment tolerance, and beta_n and the
-# parameters at 10x their measured errors.
+# t~_n moves beta_n against it, kappa amplifies both).  The state itself,
+# beta_n t~_n / psi on the reference samples (the Krylov column B_n, in the
+# mean-square norm), is invariant under the scale but still measures those
+# directions pointwise on samples of |psi|^2, not of |psi_n|^2: measured
+# 30-50x the moment error (float64 CG 8.8e-5, float32 Cholesky 4.3e-5,
+# mixed 5e-3), while mu_n, its projection on the probe, stays at the bar.
+# beta_n, the parameters and the state are gated at about 10x their
+# measured errors (regression guards); the moments at the parity bar.
 # Tolerances: (mu / mu_0, beta relative, parameters relative, B_n rms relative).
 SOLVERS = {"cholesky": dict(solver="cholesky"),
            "cg": dict(solver="cg", cg_maxit=400, cg_tol=1e-10, jacobi=False),
@@ -220,12 +224,12 @@ CG_TOL = {"fp64": 1e-10, "fp32": 1e-7, "mixed": 1e-5}
 
 
 @pytest.mark.parametrize("path,tol", [("fp64-cholesky", (1e-9, 1e-9, 1e-9, 1e-9)),
-                                      ("fp64-cg", (1e-5, 1e-3, 1e-3, 1e-5)),
-                                      ("fp64-pcg", (1e-4, 1e-2, 1e-2, 1e-4)),
-                                      ("fp32-cholesky", (1e-5, 1e-2, 1e-2, 1e-5)),
-                                      ("fp32-pcg", (1e-5, 1e-2, 1e-2, 1e-5)),
-                                      ("mixed-cg", (1e-3, 0.5, 0.2, 1e-3)),
-                                      ("mixed-pcg", (1e-3, 0.5, 0.2, 1e-3))])
+                                      ("fp64-cg", (1e-5, 5e-3, 1e-3, 1e-3)),
+                                      ("fp64-pcg", (1e-4, 2e-2, 5e-3, 5e-3)),
+                                      ("fp32-cholesky", (1e-5, 5e-3, 2e-3, 5e-4)),
+                                      ("fp32-pcg", (1e-5, 1e-2, 1e-2, 3e-3)),
+                                      ("mixed-cg", (1e-3, 0.2, 0.2, 5e-2)),
+                                      ("mixed-pcg", (1e-3, 0.2, 0.2, 5e-2))])
 def test_single_projection_step_replay(e0, recorded, path, tol):
     from paper_2103_08804_gb300 import api
     prec_s, sol = path.split("-")
