@@ -19,8 +19,18 @@
 // p . Ap reduction.  The CG is Hestenes-Stiefel from x = 0, optionally with
 // the Jacobi preconditioner diag(S) + lambda, stopping at |r| <= tol |F|.
 //
-// Per CG iteration (three grid barriers):
-//   W   walker phase (each CTA its walker range):
+// The CG is the Chronopoulos-Gear form of Hestenes-Stiefel CG (Chronopoulos
+// and Gear, J. Comput. Appl. Math. 25, 1989): with u = M^-1 r and w = A u,
+//   gamma = (r, u), delta = (u, A u), beta = gamma / gamma_prev,
+//   alpha = gamma / (delta - beta gamma / alpha_prev),
+//   p = u + beta p, s = w + beta s (s = A p), x += alpha p, r -= alpha s,
+// the same iterates as the textbook recursion in exact arithmetic, with both
+// inner products of an iteration formed together: delta comes out of the
+// walker phase (the centred form above) and gamma from the slice phase, so
+// an iteration needs two grid barriers.
+//
+// Per CG iteration:
+//   W   walker phase (each CTA its walker range), the product A u:
 //       W1: D1 = sigma V on the tensor cores (A = sigma tile [128 walkers x
 //           32 sites] exact in bf16, B = three bf16 planes of V [256 columns
 //           (Re/Im of 128 hidden units) x 32 sites], streamed by bulk copies
@@ -31,11 +41,12 @@
 //           accumulated over the CTA's walkers, then written as the CTA's
 //           partial row; the a- and b-sums on the CUDA cores.
 //   |   grid barrier
-//   C   each CTA its slice of P: S p from the partial rows (Kahan-compensated
-//       float32 sums in a fixed order), alpha, x += alpha p, r -= alpha S p.
+//   S   each CTA its slice of P: A u from the partial rows (Kahan-compensated
+//       float32 sums in a fixed order), alpha, beta, the updates of p, s, x,
+//       r, the new u and its bf16 planes, the partial inner products.
 //   |   grid barrier
-//   P   convergence test; beta; p = z + beta p; the bf16 planes of the new p.
-//   |   grid barrier
+// The convergence test |r| <= tol |F| opens each walker phase; the operand
+// copies of that phase start before it, the MMAs after it.
 //
 // Warp 0 (one thread) issues the bulk copies and the MMAs; warps 1-8
 // ("compute warps") do everything else.  Every wait is bounded: a wait that
@@ -57,7 +68,8 @@ constexpr int W1_STAGE = W1_A + 3 * W1_B_PLANE; // 56 KB
 constexpr int Y_BLK = 128 * 32 * 2;             // one plane of one 128-column n-block
 constexpr uint32_t WAIT_LIMIT = 1u << 26;       // mbarrier polls
 constexpr unsigned BAR_LIMIT = 1u << 23;        // grid-barrier polls (~1 s with the sleeps)
-constexpr int MAX_WPC = 1024;                   // walkers per CTA
+constexpr int MAX_WPC = 512;                    // walkers per CTA
+constexpr int KS_MAX = 512;                     // parameters per CTA (its CG slice in smem)
 
 struct Geo {
     int N, M, P, B;
@@ -102,8 +114,8 @@ struct Args {
     int* status;
 };
 
-// scalar partial slots
-enum { S_WW = 0, S_RR = 1, S_RZ = 2, S_FF = 3, S_OPR = 4, S_OPI = 5, S_PP = 6 };
+// scalar partial slots, one value per CTA: psc[cta * 8 + slot]
+enum { S_WW = 0, S_RR = 1, S_GAM = 2, S_FF = 3, S_OUR = 4, S_OUI = 5, S_UU = 6 };
 
 CR_D void split3(float x, __nv_bfloat16* hi, __nv_bfloat16* mid, __nv_bfloat16* lo) {
     *hi = __float2bfloat16_rn(x);
@@ -135,12 +147,6 @@ CR_D void kadd(float& s, float& c, float v) {
     s = t;
 }
 
-CR_D unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // generic-proxy global writes -> visible to later bulk copies (async proxy)
 CR_D void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
 
@@ -165,6 +171,13 @@ CR_HD size_t v2_offset(const Geo& g, int n, int i) {
 
 struct Smem {
     unsigned char* ring;
+    // the CTA's slice of the CG vectors, resident for the whole solve
+    cpx<double>* x;     // [KS_MAX]
+    cpx<double>* r;
+    cpx<double>* p;
+    cpx<double>* sv;    // s = A p
+    cpx<double>* ob;    // Obar_k = (sum_s O_sk) / B
+    double* d;          // Jacobi diagonal (1 without preconditioning)
     cpx<float>* wbuf;   // [wpc] centred u of the CTA's walkers
     cpx<float>* va;     // [N]
     cpx<float>* vb;     // [M]
@@ -177,12 +190,25 @@ struct Smem {
 };
 
 // mbarrier indices
-enum { FULL1 = 0, EMPTY1 = 3, D1FULL = 6, D1EMPTY = 8, FULL2 = 10, EMPTY2 = 12, D2FULL = 14, NMB = 15 };
+enum { FULL1 = 0, EMPTY1 = 3, D1FULL = 6, D1EMPTY = 8, FULL2 = 10, EMPTY2 = 12, D2FULL = 14, GO = 15,
+       NMB = 16 };
 
 CR_D Smem carve(unsigned char* sm, const Geo& g) {
     Smem s;
     s.ring = sm;
     unsigned char* p = sm + g.ring;
+    s.x = (cpx<double>*)p;
+    p += KS_MAX * 16;
+    s.r = (cpx<double>*)p;
+    p += KS_MAX * 16;
+    s.p = (cpx<double>*)p;
+    p += KS_MAX * 16;
+    s.sv = (cpx<double>*)p;
+    p += KS_MAX * 16;
+    s.ob = (cpx<double>*)p;
+    p += KS_MAX * 16;
+    s.d = (double*)p;
+    p += KS_MAX * 8;
     s.wbuf = (cpx<float>*)p;
     p += (size_t)MAX_WPC * 8;
     s.va = (cpx<float>*)p;
@@ -226,11 +252,10 @@ CR_D bool grid_sync(unsigned* bar, unsigned target, volatile int* flag, int* sta
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&bar[0], 1u);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;\n" ::"l"(&bar[0]) : "memory");
         unsigned n = 0;
         for (;;) {
-            if (ld_acquire(&bar[0]) >= target) break;
+            if (*(volatile unsigned*)&bar[0] >= target) break;
             if (*(volatile unsigned*)&bar[1]) {
                 flag[0] = 1;
                 break;
@@ -241,39 +266,57 @@ CR_D bool grid_sync(unsigned* bar, unsigned target, volatile int* flag, int* sta
                 set_status(status, CR_ETIMEOUT);
                 break;
             }
-            __nanosleep(64);
+            if (n > 4096) __nanosleep(64);  // spin first: most waits are a few microseconds
         }
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;\n" ::: "memory");  // acquire what the others released
     }
     __syncthreads();
     tc::fence_after_sync();
     return flag[0] == 0;
 }
 
-// Sum of v over the 256 compute threads (float64), result in every one.
-CR_D double csum(double v, double* red) {
-    v = warp_sum(v);
+// The CTA's partials of NV scalar slots (compute threads only): warp sums,
+// then one barrier, then the eight warp values of each slot added in a
+// fixed tree order and written to psc[cta * 8 + slot].
+template <int NV>
+CR_D void put_psc(double* psc, int cta, const double (&v)[NV], const int (&sl)[NV], double* red) {
     const int cw = (threadIdx.x >> 5) - 1, lane = threadIdx.x & 31;
-    compute_sync();
-    if (lane == 0) red[cw] = v;
-    compute_sync();
-    double t = 0.0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) t += red[w];
+    for (int q = 0; q < NV; ++q) {
+        const double w = warp_sum(v[q]);
+        if (lane == 0) red[cw * 8 + q] = w;
+    }
     compute_sync();
-    return t;
+    const int ct = threadIdx.x - 32;
+    if (ct < NV) {
+        const double* r = red + ct;
+        const double tot = ((r[0] + r[8]) + (r[16] + r[24])) + ((r[32] + r[40]) + (r[48] + r[56]));
+        psc[(size_t)cta * 8 + sl[ct]] = tot;
+    }
 }
 
-// sum over CTAs of scalar partial slot `sl`, fixed order (identical in every CTA)
-CR_D double sum_psc(const double* psc, int G, int sl) {
+// Sums over all CTAs of NV slots, by one warp, all loads in flight at once,
+// in a fixed order (the same values in every lane and every CTA).
+template <int NV>
+CR_D void sum_psc(const double* psc, int G, const int (&sl)[NV], double (&out)[NV]) {
     const int lane = threadIdx.x & 31;
-    double v = 0.0;
-    for (int c = lane; c < G; c += 32) v += psc[(size_t)c * 8 + sl];
-    return warp_sum(v);
+    double v[NV][5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const int cc = lane + 32 * m;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q][m] = cc < G ? psc[(size_t)cc * 8 + sl[q]] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double x = (v[q][0] + v[q][1]) + (v[q][2] + v[q][3]);
+        for (int cc = lane + 160; cc < G; cc += 32) x += psc[(size_t)cc * 8 + sl[q]];
+        out[q] = warp_sum(x + v[q][4]);
+    }
 }
 
-// The operands of p_k (value pk) for the walker phase: float32 a/b parts,
-// bf16 planes of the W part.  Also accumulates Obar . p and |p|^2.
+// The operands of entry k (value pk) of the vector the walker phase
+// multiplies: float32 a- and b-parts, three bf16 planes of the W part.
 CR_D void emit_p(const Args& a, int k, cpx<double> pk) {
     const Geo& g = a.g;
     const int N = g.N, M = g.M;
@@ -300,14 +343,11 @@ __global__ void __launch_bounds__(FC_THREADS, 1) cg_fused_kernel(const __grid_co
     const int c = blockIdx.x, t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int ct = t - 32;  // compute-thread index (warps 1-8)
     Smem s = carve(sm_raw, g);
-    volatile int* flag = s.flag;
+    volatile int* flag = s.flag;  // [0] CTA abort, [1] solve finished
     const int s0 = c * g.wpc, s1 = min(B, s0 + g.wpc), nw = max(0, s1 - s0);
     const int k0 = min(P, c * g.kslice), k1 = min(P, k0 + g.kslice);
     cpx<double>* X = (cpx<double>*)a.cg;
-    cpx<double>* Rv = X + P;
-    cpx<double>* Pv = X + 2 * P;
     cpx<double>* Ap = X + 3 * P;
-    cpx<double>* Dg = X + 4 * P;
     const double invB = 1.0 / B;
 
     if (t == 0) {
@@ -358,123 +398,142 @@ __global__ void __launch_bounds__(FC_THREADS, 1) cg_fused_kernel(const __grid_co
             *reinterpret_cast<uint4*>(a.b2 + ((size_t)c * g.nwc + wc) * g.Np * 64 + koff(i, q8 * 8)) =
                 pack8(v);
         }
-        // phase P0 on this CTA's slice: x = 0, r = F, z = r / d, p = z
-        // (apply_only: p = v), and the operands of p
-        double ff = 0.0, rz = 0.0, opr = 0.0, opi = 0.0, pp = 0.0;
+        // this CTA's slice: x = 0, r = F, p = s = 0, u = r / d (apply_only:
+        // u = v), the operands of u and the partial inner products
+        double ff = 0.0, gam = 0.0, our = 0.0, oui = 0.0, uu = 0.0;
         for (int k = k0 + ct; k < k1; k += NCT) {
-            cpx<double> pk;
+            const int kl = k - k0;
+            const cpx<double> obk = invB * a.sO[k];
+            s.ob[kl] = obk;
+            cpx<double> uk;
             if (a.apply_only) {
-                pk = a.v_in[k];
+                uk = a.v_in[k];
+                s.r[kl] = uk;
+                s.d[kl] = 1.0;
             } else {
                 double d = 1.0;
                 if (a.precond) {
                     const double o2 = k < N ? 1.0
                                             : invB * a.sO[P + 2 + (k < N + M ? k - N : (k - N - M) % M)].x;
-                    d = o2 - abs2(invB * a.sO[k]) + a.shift;
+                    d = o2 - abs2(obk) + a.shift;
                 }
                 const cpx<double> f = a.F[k];
-                pk = (1.0 / d) * f;
-                X[k] = {0.0, 0.0};
-                Rv[k] = f;
-                Dg[k] = {d, 0.0};
+                uk = (1.0 / d) * f;
+                s.x[kl] = {0.0, 0.0};
+                s.r[kl] = f;
+                s.d[kl] = d;
                 ff += abs2(f);
-                rz += cmulc(f, pk).x;
+                gam += cmulc(f, uk).x;
             }
-            Pv[k] = pk;
-            emit_p(a, k, pk);
-            const cpx<double> ob = (invB * a.sO[k]) * pk;
-            opr += ob.x;
-            opi += ob.y;
-            pp += abs2(pk);
+            s.p[kl] = {0.0, 0.0};
+            s.sv[kl] = {0.0, 0.0};
+            emit_p(a, k, uk);
+            const cpx<double> ou = obk * uk;
+            our += ou.x;
+            oui += ou.y;
+            uu += abs2(uk);
         }
         fence_proxy_async_global();
-        ff = csum(ff, s.red);
-        rz = csum(rz, s.red);
-        opr = csum(opr, s.red);
-        opi = csum(opi, s.red);
-        pp = csum(pp, s.red);
-        if (ct == 0) {
-            double* ps = a.psc + (size_t)c * 8;
-            ps[S_FF] = ff;
-            ps[S_RZ] = rz;
-            ps[S_OPR] = opr;
-            ps[S_OPI] = opi;
-            ps[S_PP] = pp;
-        }
-        fence_proxy_async_global();
+        const double pv[6] = {ff, ff, gam, our, oui, uu};
+        const int ps[6] = {S_FF, S_RR, S_GAM, S_OUR, S_OUI, S_UU};
+        put_psc<6>(a.psc, c, pv, ps, s.red);
     }
     unsigned round = 1;
     bool ok = grid_sync(a.bar, round++ * G, flag, a.status);
     const uint32_t taddr = *s.slot;
 
-    // scalars common to all CTAs (warp 1 sums, broadcast through shared memory)
-    if (warp == 1) {
-        const double ff = sum_psc(a.psc, G, S_FF), rz = sum_psc(a.psc, G, S_RZ);
-        if (lane == 0) {
-            s.bc[0] = ff;
-            s.bc[1] = rz;
-        }
-    }
-    __syncthreads();
-    const double ff = s.bc[0];
-    double rz = s.bc[1];
-    int its = 0, done = (!a.apply_only && ff == 0.0) ? 1 : 0;
-    double rr = ff;
+    int its = 0, done = 0;
+    double ff = 0.0, rr = 0.0, gam = 0.0, gam_prev = 1.0, alpha_prev = 1.0;
     // pipeline counters (identical in every role of the CTA)
     uint32_t g1 = 0, u1 = 0, g2 = 0, u2 = 0;
     // producer only: last copy issued into each stage and last MMA commit, so
     // that an abort can wait (bounded) for what is still in flight
     int last1[NS1] = {-1, -1, -1}, last2[2] = {-1, -1}, lastm1 = -1, lastm2 = -1;
+    const int units = g.ntpc * g.npass1;
+    const int total1 = units * g.nkc1;
+    auto width_of = [&](int ps) { return ps < g.npass1 - 1 ? 256 : g.wlast1; };
 
-    while (ok && !done && its < (a.apply_only ? 1 : a.maxit)) {
+    while (ok) {
         // ======================================================= walker phase
+        // producer: W1 operand copies start at once (their data was released
+        // before the barrier); the MMAs wait for the convergence decision
+        auto load1 = [&](int q) {
+            const uint32_t gq = g1 + q, b = gq % NS1;
+            if (gq >= NS1 && !wait_mb(&s.mb[EMPTY1 + b], ((gq / NS1) - 1) & 1, flag, a.bar, a.status))
+                return;
+            const int unit = q / g.nkc1, kc = q % g.nkc1;
+            const int tt = unit / g.npass1, ps = unit % g.npass1, w = width_of(ps);
+            unsigned char* st = s.ring + (size_t)b * W1_STAGE;
+            tc::mbar_expect_tx(&s.mb[FULL1 + b], (uint32_t)(W1_A + 3 * w * 64));
+            tc::bulk_g2s(st, a.a1 + ((size_t)(c * g.ntpc + tt) * g.nkc1 + kc) * W1_A, W1_A,
+                         &s.mb[FULL1 + b]);
+            const size_t boff = ((size_t)256 * ps * g.Kp + (size_t)w * 32 * kc) * 2;
+            for (int pl = 0; pl < 3; ++pl)
+                tc::bulk_g2s(st + W1_A + pl * W1_B_PLANE, a.v2 + pl * a.v2_plane + boff,
+                             (uint32_t)(w * 64), &s.mb[FULL1 + b]);
+            last1[b] = (int)gq;
+        };
+        const int npre = NS1 - 1 < total1 ? NS1 - 1 : total1;
+        if (t == 0)
+            for (int q = 0; q < npre; ++q) load1(q);
         if (warp == 1) {
-            const double opr = sum_psc(a.psc, G, S_OPR), opi = sum_psc(a.psc, G, S_OPI);
-            const double pp = sum_psc(a.psc, G, S_PP);
+            // the inner products of the current r and u, and the decision
+            const int sl6[6] = {S_RR, S_GAM, S_OUR, S_OUI, S_UU, S_FF};
+            double v6[6];
+            sum_psc<6>(a.psc, G, sl6, v6);
+            const double r2 = v6[0], gm = v6[1], our = v6[2], oui = v6[3], uu = v6[4], f2 = v6[5];
             if (lane == 0) {
-                s.bc[2] = opr;  // ubar = Obar . p
-                s.bc[3] = opi;
-                s.bc[4] = pp;
+                if (its == 0) s.bc[0] = f2;
+                const double fnorm2 = s.bc[0];
+                const int conv = !a.apply_only && !(r2 > a.tol * a.tol * fnorm2);
+                // the decision of the whole CTA: converged, out of iterations, or aborted
+                const int fin = conv || (!a.apply_only && its >= a.maxit) || flag[0];
+                s.bc[7] = conv;
+                s.bc[1] = r2;
+                s.bc[2] = our;  // ubar = Obar . u
+                s.bc[3] = oui;
+                s.bc[4] = uu;
+                s.bc[6] = gm;
+                flag[1] = fin;
+                mbar_arrive(&s.mb[GO]);
             }
         }
         if (ct >= 0) {
             for (int i = ct; i < N; i += NCT) s.va[i] = a.vab[i];
             for (int j = ct; j < M; j += NCT) s.vb[j] = a.vab[N + j];
         }
-        __syncthreads();
+        // the decision reaches warp 0 through GO, the compute warps through
+        // their barrier; flag[1], written once before either, is uniform
+        if (warp == 0) wait_mb(&s.mb[GO], (uint32_t)its & 1, flag, a.bar, a.status);
+        if (ct >= 0) compute_sync();
+        ff = s.bc[0];
+        rr = s.bc[1];
+        gam = s.bc[6];
+        if (flag[1]) {
+            // finished: let the copies issued above land, then leave
+            if (t == 0)
+                for (int q = 0; q < npre; ++q) {
+                    const uint32_t gq = g1 + q;
+                    tc::mbar_wait(&s.mb[FULL1 + gq % NS1], (gq / NS1) & 1, WAIT_LIMIT);
+                }
+            done = s.bc[7] != 0.0;
+            __syncthreads();
+            break;
+        }
         const cpx<double> ubar = {s.bc[2], s.bc[3]};
         const cpx<float> ubar32 = ccast<float>(ubar);
-        const int units = g.ntpc * g.npass1;
-        double ww = 0.0;  // sum |w_s|^2 of this CTA (compute threads)
+        const double uu = s.bc[4];
+        double ww = 0.0;  // sum |w_s|^2 of this thread's walkers
         if (warp == 0) {
             if (lane == 0) {
                 // ----------------------------------------- W1 producer / MMA
-                const int total = units * g.nkc1;
-                auto width_of = [&](int ps) { return ps < g.npass1 - 1 ? 256 : g.wlast1; };
-                auto load = [&](int q) {
-                    const uint32_t gq = g1 + q, b = gq % NS1;
-                    if (gq >= NS1 && !wait_mb(&s.mb[EMPTY1 + b], ((gq / NS1) - 1) & 1, flag, a.bar, a.status))
-                        return;
-                    const int unit = q / g.nkc1, kc = q % g.nkc1;
-                    const int tt = unit / g.npass1, ps = unit % g.npass1, w = width_of(ps);
-                    unsigned char* st = s.ring + (size_t)b * W1_STAGE;
-                    tc::mbar_expect_tx(&s.mb[FULL1 + b], (uint32_t)(W1_A + 3 * w * 64));
-                    tc::bulk_g2s(st, a.a1 + ((size_t)(c * g.ntpc + tt) * g.nkc1 + kc) * W1_A, W1_A,
-                                 &s.mb[FULL1 + b]);
-                    const size_t boff = ((size_t)256 * ps * g.Kp + (size_t)w * 32 * kc) * 2;
-                    for (int pl = 0; pl < 3; ++pl)
-                        tc::bulk_g2s(st + W1_A + pl * W1_B_PLANE, a.v2 + pl * a.v2_plane + boff,
-                                     (uint32_t)(w * 64), &s.mb[FULL1 + b]);
-                    last1[b] = (int)gq;
-                };
-                for (int q = 0; q < NS1 - 1 && q < total; ++q) load(q);
-                for (int q = 0; q < total; ++q) {
-                    if (q + NS1 - 1 < total) load(q + NS1 - 1);
+                for (int q = 0; q < total1; ++q) {
+                    if (q + NS1 - 1 < total1 && q + NS1 - 1 >= npre) load1(q + NS1 - 1);
                     const uint32_t gq = g1 + q, b = gq % NS1;
                     const int unit = q / g.nkc1, kc = q % g.nkc1, ps = unit % g.npass1;
-                    const uint32_t uu = u1 + unit, h = uu & 1;
-                    if (kc == 0 && uu >= 2)
-                        wait_mb(&s.mb[D1EMPTY + h], ((uu >> 1) - 1) & 1, flag, a.bar, a.status);
+                    const uint32_t uu1 = u1 + unit, h = uu1 & 1;
+                    if (kc == 0 && uu1 >= 2)
+                        wait_mb(&s.mb[D1EMPTY + h], ((uu1 >> 1) - 1) & 1, flag, a.bar, a.status);
                     wait_mb(&s.mb[FULL1 + b], (gq / NS1) & 1, flag, a.bar, a.status);
                     tc::fence_after_sync();
                     const int w = width_of(ps);
@@ -498,37 +557,79 @@ __global__ void __launch_bounds__(FC_THREADS, 1) cg_fused_kernel(const __grid_co
         } else {
             // --------------------------------------------- W1 compute warps
             const int lb = warp & 3, hf = (warp - 1) >> 2, row = 32 * lb + lane;
+            const bool vecT = (M & 1) == 0;
             cpx<float> uacc = {0.f, 0.f};
             for (int unit = 0; unit < units; ++unit) {
                 const int tt = unit / g.npass1, ps = unit % g.npass1;
-                const uint32_t uu = u1 + unit, h = uu & 1;
+                const uint32_t uu1 = u1 + unit, h = uu1 & 1;
                 const int sl = tt * g.trows + row;
                 const bool valid = row < g.trows && sl < nw;
                 const int sw = s0 + sl;
+                const cpx<float>* Tr = a.T + (size_t)sw * M;
+                const int w = width_of(ps), ngr = w / 16;
+                // T of a 16-column group (8 hidden units) as four 16-byte
+                // loads, fetched two groups ahead of its use
+                auto fetchT = [&](int grp, float4* tv) {
+                    const int j0 = 128 * ps + 8 * grp;
+                    if (grp >= ngr || !valid) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) tv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else if (vecT && j0 + 8 <= M) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            tv[q] = __ldg(reinterpret_cast<const float4*>(Tr + j0) + q);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int j = j0 + 2 * q;
+                            const cpx<float> t0 = j < M ? ldg(Tr + j) : cpx<float>{0.f, 0.f};
+                            const cpx<float> t1 = j + 1 < M ? ldg(Tr + j + 1) : cpx<float>{0.f, 0.f};
+                            tv[q] = make_float4(t0.x, t0.y, t1.x, t1.y);
+                        }
+                    }
+                };
+                float4 tc0[4], tc1[4], tc2[4];
+                fetchT(hf, tc0);
+                fetchT(hf + 2, tc1);
                 if (ps == 0) {
-                    // sigma . va: the two threads of a row take alternate sites
+                    // sigma . va: the two threads of a row take alternate
+                    // 16-site blocks of the row (16-byte loads when N % 16 == 0)
                     uacc = {0.f, 0.f};
-                    if (valid)
-                        for (int i = hf; i < N; i += 2)
-                            uacc = uacc + (float)a.spins[(size_t)sw * N + i] * s.va[i];
+                    if (valid) {
+                        const int8_t* sr = a.spins + (size_t)sw * N;
+                        if ((N & 15) == 0) {
+                            for (int b16 = hf; b16 < N / 16; b16 += 2) {
+                                const int4 raw = __ldg(reinterpret_cast<const int4*>(sr) + b16);
+                                const int8_t* sv = reinterpret_cast<const int8_t*>(&raw);
+#pragma unroll
+                                for (int q = 0; q < 16; ++q)
+                                    uacc = uacc + (float)sv[q] * s.va[16 * b16 + q];
+                            }
+                        } else {
+                            for (int i = hf; i < N; i += 2) uacc = uacc + (float)sr[i] * s.va[i];
+                        }
+                    }
                 }
-                wait_mb(&s.mb[D1FULL + h], (uu >> 1) & 1, flag, a.bar, a.status);
+                wait_mb(&s.mb[D1FULL + h], (uu1 >> 1) & 1, flag, a.bar, a.status);
                 tc::fence_after_sync();
-                const int w = ps < g.npass1 - 1 ? 256 : g.wlast1;
-                for (int grp = hf; grp < w / 16; grp += 2) {
+                for (int grp = hf; grp < ngr; grp += 2) {
+                    fetchT(grp + 4, tc2);
                     float d[16];
                     tc::tmem_ld16(taddr + ((uint32_t)(32 * lb) << 16) + 256 * h + 16 * grp, d);
                     const int j0 = 128 * ps + 8 * grp;
-                    if (valid) {
-                        const cpx<float>* Tr = a.T + (size_t)sw * M;
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int j = j0 + q;
-                            if (j < M) {
-                                const cpx<float> x = {d[2 * q] + s.vb[j].x, d[2 * q + 1] + s.vb[j].y};
-                                uacc = uacc + ldg(Tr + j) * x;
-                            }
-                        }
+                    for (int q = 0; q < 8; ++q) {
+                        const int j = j0 + q;
+                        const int jv = j < M ? j : 0;
+                        const float4 tq = tc0[q >> 1];
+                        const cpx<float> tj = (q & 1) ? cpx<float>{tq.z, tq.w} : cpx<float>{tq.x, tq.y};
+                        const cpx<float> x = {d[2 * q] + s.vb[jv].x, d[2 * q + 1] + s.vb[jv].y};
+                        uacc = uacc + tj * x;  // tj = 0 past M and on invalid rows
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        tc0[q] = tc1[q];
+                        tc1[q] = tc2[q];
                     }
                 }
                 tc::fence_before_sync();
@@ -550,24 +651,72 @@ __global__ void __launch_bounds__(FC_THREADS, 1) cg_fused_kernel(const __grid_co
                     compute_sync();
                 }
             }
-            // a-sums: sum_s sigma_si w_s per site (Kahan), into the partial row
+        }
+        g1 += total1;
+        u1 += units;
+        // TMEM: every D1 read is done before the W2 MMAs reuse the columns
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+
+        // a-sums: sum_s sigma_si w_s per site.  Thread (block b16 of 16 sites,
+        // walker subset sub) sums its walkers from 16-byte spin loads, eight
+        // walkers' loads in flight; each site's nsub partial sums are then
+        // added in a fixed order, through the operand ring (idle here).
+        if (ct >= 0) {
+            const int NG = (N + 15) / 16, nsub = NCT / NG;
+            const int b16 = ct % NG, sub = ct / NG;
+            cpx<float>* xa = (cpx<float>*)s.ring;  // [nsub][NG * 16]
+            if (sub < nsub) {
+                float ax[16], ay[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) ax[q] = ay[q] = 0.f;
+                for (int sl0 = sub; sl0 < nw; sl0 += 8 * nsub) {
+                    int4 raw[8];
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const int sl = sl0 + m * nsub;
+                        const int8_t* sr = a.spins + (size_t)(s0 + (sl < nw ? sl : 0)) * N;
+                        if (sl >= nw) {
+                            raw[m] = make_int4(0, 0, 0, 0);
+                        } else if ((N & 15) == 0) {
+                            raw[m] = __ldg(reinterpret_cast<const int4*>(sr) + b16);
+                        } else {
+                            int8_t sv[16];
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) sv[q] = 16 * b16 + q < N ? sr[16 * b16 + q] : (int8_t)0;
+                            memcpy(&raw[m], sv, 16);
+                        }
+                    }
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const int sl = sl0 + m * nsub;
+                        const cpx<float> wv = sl < nw ? s.wbuf[sl] : cpx<float>{0.f, 0.f};
+                        const int8_t* sv = reinterpret_cast<const int8_t*>(&raw[m]);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            ax[q] = fmaf((float)sv[q], wv.x, ax[q]);
+                            ay[q] = fmaf((float)sv[q], wv.y, ay[q]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) xa[sub * NG * 16 + 16 * b16 + q] = {ax[q], ay[q]};
+            }
             compute_sync();
             for (int i = ct; i < N; i += NCT) {
                 float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
-                for (int sl = 0; sl < nw; ++sl) {
-                    const float sg = (float)a.spins[(size_t)(s0 + sl) * N + i];
-                    kadd(sx, cx, sg * s.wbuf[sl].x);
-                    kadd(sy, cy, sg * s.wbuf[sl].y);
+                for (int r = 0; r < nsub; ++r) {
+                    const cpx<float> v = xa[r * NG * 16 + i];
+                    kadd(sx, cx, v.x);
+                    kadd(sy, cy, v.y);
                 }
                 a.part[2 * ((size_t)c * P + i)] = sx - cx;
                 a.part[2 * ((size_t)c * P + i) + 1] = sy - cy;
             }
         }
-        g1 += units * g.nkc1;
-        u1 += units;
-        // TMEM: every D1 read is done before the W2 MMAs reuse the columns
         tc::fence_before_sync();
-        __syncthreads();
+        __syncthreads();  // the ring is W2's from here
         tc::fence_after_sync();
 
         for (int ps2 = 0; ps2 < g.npass2; ++ps2) {
@@ -617,19 +766,40 @@ __global__ void __launch_bounds__(FC_THREADS, 1) cg_fused_kernel(const __grid_co
                 // ---------------------------------------- W2 compute warps
                 const int tpj = NCT / Jp;  // threads per hidden unit: 2 or 4
                 const int j = jp0 + ct % Jp;
+                const int ng = 4 / tpj;    // walker groups of 8 per thread and chunk (1 or 2)
                 float bsx = 0.f, bsy = 0.f, bcx = 0.f, bcy = 0.f;
+                // T of this thread's walkers of a chunk, fetched one chunk ahead
+                // (compile-time indices throughout, so the buffers stay in registers)
+                cpx<float> tcur[2][8], tnxt[2][8];
+#define FCG_FETCH_T(WC, TV)                                                                       \
+    _Pragma("unroll") for (int gi = 0; gi < 2; ++gi) {                                            \
+        const int grp = ct / Jp + gi * tpj;                                                       \
+        _Pragma("unroll") for (int q = 0; q < 8; ++q) {                                           \
+            const int sl = (WC) * 32 + grp * 8 + q;                                               \
+            TV[gi][q] = (gi < ng && sl < nw && j < M) ? ldg(a.T + (size_t)(s0 + sl) * M + j)       \
+                                                      : cpx<float>{0.f, 0.f};                     \
+        }                                                                                         \
+    }
+                FCG_FETCH_T(0, tcur)
                 for (int wc = 0; wc < g.nwc; ++wc) {
                     const uint32_t gq = g2 + wc, b = gq & 1;
+                    if (wc + 1 < g.nwc) {
+                        FCG_FETCH_T(wc + 1, tnxt)
+                    }
                     if (gq >= 2) wait_mb(&s.mb[EMPTY2 + b], ((gq >> 1) - 1) & 1, flag, a.bar, a.status);
                     tc::fence_after_sync();
                     unsigned char* sy = s.ring + b * stage2;
-                    for (int grp = ct / Jp; grp < 4; grp += tpj) {
+#pragma unroll
+                    for (int gi = 0; gi < 2; ++gi) {
+                        if (gi >= ng) break;
+                        const int grp = ct / Jp + gi * tpj;
                         __nv_bfloat16 h[2][8], m[2][8], l[2][8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const int sl = wc * 32 + grp * 8 + q;
-                            cpx<float> y = {0.f, 0.f};
-                            if (sl < nw && j < M) y = conj(ldg(a.T + (size_t)(s0 + sl) * M + j)) * s.wbuf[sl];
+                            // walkers past the CTA's range contribute exact zeros (their
+                            // slots of wbuf are never written)
+                            const cpx<float> y = sl < nw ? conj(tcur[gi][q]) * s.wbuf[sl] : cpx<float>{0.f, 0.f};
                             kadd(bsx, bcx, y.x);
                             kadd(bsy, bcy, y.y);
                             split3(y.x, &h[0][q], &m[0][q], &l[0][q]);
@@ -646,7 +816,12 @@ __global__ void __launch_bounds__(FC_THREADS, 1) cg_fused_kernel(const __grid_co
                     }
                     tc::fence_proxy_async();
                     mbar_arrive(&s.mb[FULL2 + b]);
+#pragma unroll
+                    for (int gi = 0; gi < 2; ++gi)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) tcur[gi][q] = tnxt[gi][q];
                 }
+#undef FCG_FETCH_T
                 // the pass's D2^T rows -> partial row (W part); b-sums
                 wait_mb(&s.mb[D2FULL], u2 & 1, flag, a.bar, a.status);
                 tc::fence_after_sync();
@@ -681,35 +856,51 @@ __global__ void __launch_bounds__(FC_THREADS, 1) cg_fused_kernel(const __grid_co
             tc::fence_after_sync();
         }
         if (ct >= 0) {
-            ww = csum(ww, s.red);
-            if (ct == 0) a.psc[(size_t)c * 8 + S_WW] = ww;
+            const double pv[1] = {ww};
+            const int ps[1] = {S_WW};
+            put_psc<1>(a.psc, c, pv, ps, s.red);
         }
         ok = grid_sync(a.bar, round++ * G, flag, a.status);
         if (!ok) break;
 
-        // ================================================ phase C (slice)
+        // ================================================= slice phase
         if (warp == 1) {
-            const double sww = sum_psc(a.psc, G, S_WW);
-            if (lane == 0) s.bc[5] = sww;
+            const int sl1[1] = {S_WW};
+            double v1[1];
+            sum_psc<1>(a.psc, G, sl1, v1);
+            if (lane == 0) s.bc[5] = v1[0];
         }
         __syncthreads();
-        const double pAp = s.bc[5] * invB + a.shift * s.bc[4];
-        const double alpha = a.apply_only ? 0.0 : rz / pAp;
-        double rrp = 0.0, rzp = 0.0;
+        // delta = (u, A u) = (1/B) sum_s |w_s|^2 + lambda |u|^2
+        const double delta = s.bc[5] * invB + a.shift * uu;
+        const double beta = its == 0 ? 0.0 : gam / gam_prev;
+        const double alpha = its == 0 ? gam / delta : gam / (delta - beta * gam / alpha_prev);
         if (ct >= 0) {
+            double r2 = 0.0, gm = 0.0, our = 0.0, oui = 0.0, u2s = 0.0;
             const int L = k1 - k0;
             const int tpk = L <= 64 ? 4 : (L <= 128 ? 2 : 1);
             const int cg = ct % tpk, per = NCT / tpk;
             const cpx<double> du = ubar - ccast<double>(ubar32);
+            constexpr int BATCH = 40;
             for (int base = 0; base < L; base += per) {
                 const int kk = base + ct / tpk, k = k0 + kk;
                 double tx = 0.0, ty = 0.0;
                 if (kk < L) {
                     float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
-                    for (int cc = cg; cc < G; cc += tpk) {
-                        const float2 v = *reinterpret_cast<const float2*>(a.part + 2 * ((size_t)cc * P + k));
-                        kadd(sx, cx, v.x);
-                        kadd(sy, cy, v.y);
+                    // rows cg, cg + tpk, ... with BATCH loads in flight
+                    for (int cb = cg; cb < G; cb += BATCH * tpk) {
+                        float2 v[BATCH];
+#pragma unroll
+                        for (int q = 0; q < BATCH; ++q) {
+                            const int cc = cb + q * tpk;
+                            v[q] = cc < G ? *reinterpret_cast<const float2*>(a.part + 2 * ((size_t)cc * P + k))
+                                          : make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int q = 0; q < BATCH; ++q) {
+                            kadd(sx, cx, v[q].x);
+                            kadd(sy, cy, v[q].y);
+                        }
                     }
                     tx = (double)sx - (double)cx;
                     ty = (double)sy - (double)cy;
@@ -720,74 +911,48 @@ __global__ void __launch_bounds__(FC_THREADS, 1) cg_fused_kernel(const __grid_co
                     ty += __shfl_xor_sync(0xffffffffu, ty, o);
                 }
                 if (kk < L && cg == 0) {
-                    const cpx<double> ob = invB * a.sO[k];
-                    const cpx<double> pk = Pv[k];
-                    const cpx<double> apk = invB * cpx<double>{tx, ty} - conj(ob) * du + a.shift * pk;
+                    const cpx<double> uk = (1.0 / s.d[kk]) * s.r[kk];
+                    // (A u)_k = (S + lambda) u: the centred O^dag w with the
+                    // rounding of ubar put back
+                    const cpx<double> auk =
+                        invB * cpx<double>{tx, ty} - conj(s.ob[kk]) * du + a.shift * uk;
                     if (a.apply_only) {
-                        Ap[k] = apk;
+                        Ap[k] = auk;
                     } else {
-                        X[k] = X[k] + alpha * pk;
-                        const cpx<double> rk = Rv[k] - alpha * apk;
-                        Rv[k] = rk;
-                        const double r2 = abs2(rk);
-                        rrp += r2;
-                        rzp += r2 / Dg[k].x;
+                        const cpx<double> pk = uk + beta * s.p[kk];
+                        const cpx<double> sk = auk + beta * s.sv[kk];
+                        s.p[kk] = pk;
+                        s.sv[kk] = sk;
+                        s.x[kk] = s.x[kk] + alpha * pk;
+                        const cpx<double> rk = s.r[kk] - alpha * sk;
+                        s.r[kk] = rk;
+                        const cpx<double> un = (1.0 / s.d[kk]) * rk;
+                        emit_p(a, k, un);
+                        r2 += abs2(rk);
+                        gm += cmulc(rk, un).x;
+                        const cpx<double> ou = s.ob[kk] * un;
+                        our += ou.x;
+                        oui += ou.y;
+                        u2s += abs2(un);
                     }
                 }
             }
-            rrp = csum(rrp, s.red);
-            rzp = csum(rzp, s.red);
-            if (ct == 0) {
-                a.psc[(size_t)c * 8 + S_RR] = rrp;
-                a.psc[(size_t)c * 8 + S_RZ] = rzp;
+            if (!a.apply_only) {
+                fence_proxy_async_global();
+                const double pv[5] = {r2, gm, our, oui, u2s};
+                const int ps[5] = {S_RR, S_GAM, S_OUR, S_OUI, S_UU};
+                put_psc<5>(a.psc, c, pv, ps, s.red);
             }
         }
+        gam_prev = gam;
+        alpha_prev = alpha;
         ++its;
         if (a.apply_only) break;
         ok = grid_sync(a.bar, round++ * G, flag, a.status);
-        if (!ok) break;
-
-        // ================================================ phase P (slice)
-        if (warp == 1) {
-            const double r2 = sum_psc(a.psc, G, S_RR), rzn = sum_psc(a.psc, G, S_RZ);
-            if (lane == 0) {
-                s.bc[6] = r2;
-                s.bc[7] = rzn;
-            }
-        }
-        __syncthreads();
-        rr = s.bc[6];
-        const double rz_new = s.bc[7];
-        done = !(rr > a.tol * a.tol * ff) ? 1 : 0;
-        if (done || its >= a.maxit) break;
-        const double beta = rz_new / rz;
-        rz = rz_new;
-        if (ct >= 0) {
-            double opr = 0.0, opi = 0.0, pp = 0.0;
-            for (int k = k0 + ct; k < k1; k += NCT) {
-                const cpx<double> pk = (1.0 / Dg[k].x) * Rv[k] + beta * Pv[k];
-                Pv[k] = pk;
-                emit_p(a, k, pk);
-                const cpx<double> ob = (invB * a.sO[k]) * pk;
-                opr += ob.x;
-                opi += ob.y;
-                pp += abs2(pk);
-            }
-            fence_proxy_async_global();
-            opr = csum(opr, s.red);
-            opi = csum(opi, s.red);
-            pp = csum(pp, s.red);
-            if (ct == 0) {
-                double* ps = a.psc + (size_t)c * 8;
-                ps[S_OPR] = opr;
-                ps[S_OPI] = opi;
-                ps[S_PP] = pp;
-            }
-            fence_proxy_async_global();
-        }
-        ok = grid_sync(a.bar, round++ * G, flag, a.status);
     }
 
+    if (!a.apply_only && ct >= 0)
+        for (int k = k0 + ct; k < k1; k += NCT) X[k] = s.x[k - k0];
     if (c == 0 && t == 32 && !a.apply_only) {
         a.scal[1] = ff;
         a.scal[2] = done ? 1.0 : 0.0;
@@ -821,6 +986,8 @@ static bool fcg_geometry(const cr_ctx* c, int B, Geo* g) {
     g->P = c->P;
     g->B = B;
     int G = (B + 31) / 32;
+    const int Gp = (c->P + KS_MAX - 1) / KS_MAX;  // every CTA's CG slice fits in shared memory
+    if (G < Gp) G = Gp;
     if (G > c->n_sm) G = c->n_sm;
     g->G = G;
     g->wpc = (B + G - 1) / G;
@@ -838,10 +1005,12 @@ static bool fcg_geometry(const cr_ctx* c, int B, Geo* g) {
     g->npass2 = (g->nb2 + g->nbp - 1) / g->nbp;
     g->nwc = (g->wpc + 31) / 32;
     g->kslice = (g->P + G - 1) / G;
+    if (g->kslice > KS_MAX) return false;
     const size_t r1 = (size_t)NS1 * W1_STAGE;
     const size_t r2 = 2 * ((size_t)g->nbp * 3 * Y_BLK + (size_t)g->Np * 64);
     g->ring = r1 > r2 ? r1 : r2;
-    g->smem = g->ring + (size_t)MAX_WPC * 8 + 3 * 256 * 8 + 64 * 8 + 8 * 8 + NMB * 8 + 16 + 16;
+    g->smem = g->ring + (size_t)KS_MAX * 88 + (size_t)MAX_WPC * 8 + 3 * 256 * 8 + 64 * 8 + 8 * 8 +
+              NMB * 8 + 16 + 16;
     return g->smem <= 227 * 1024;
 }
 
