@@ -1,21 +1,31 @@
 """Throughput of the RBM-Chebyshev projection step on one GB300.
 
-One step = one Chebyshev moment n of the 64-site chain workload: fit RBM_n to
+One step = one Chebyshev moment n: fit RBM_n to
 phi_n = 2 beta_{n-1} H' t~_{n-1} - beta_{n-2} t~_{n-2} by 50 natural-gradient
-iterations over 16384 walkers (each iteration: one Metropolis sweep, the local
-target R, the reductions, the matrix-free shifted solve, theta refresh),
-then beta_n = <R> and mu_n with its Krylov columns.  Inputs are synthetic
-(random complex RBM, alpha = 2, sigma = 0.02, q = pi/2) and resident in HBM;
-L2 is flushed between timed steps.
+iterations (each: one Metropolis sweep, the local target R, the estimators,
+the matrix-free shifted solve by CG, theta refresh), then beta_n = <R> and
+mu_n with its Krylov columns.  Inputs are synthetic random complex RBMs and
+seeded S^z = 0 walkers, resident in HBM; L2 is flushed between timed steps.
+
+Default workload (the largest single-GPU configuration): the 16 x 16
+periodic lattice, alpha = 1 (M = 256, P = 66,048), 65536 walkers,
+q = (pi, 0).  The mixed path (the CG as one persistent tensor-core kernel)
+is the headline; the plain float32 path is timed beside it on fewer steps;
+the moment error of the timed configuration against the float64 GPU path
+and against a converged CG is reported, and the Krylov step over 300
+states (once per sequence) is timed separately.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload chain64|batch|square10|square16|sym6]
+                  [--workload square16|chain64|batch|square10|sym6]
+
+--workload chain64: the 64-site chain (alpha = 2, 16384 walkers, q = pi/2),
+mixed and plain float32 paths, timed steps cycling through moments 3-5.
 
 --workload batch times the momentum scan instead: all 15 irreducible momenta
 of an 8 x 8 square lattice (q = 0 has a vanishing probe and is skipped) plus
 chains of 48 and 96 sites at q = pi/2, alpha = 2, 8192 walkers each; one step
 = one moment of every sequence, with every sequence's iteration in one CUDA
-graph (chunk counts autotuned), against one sequence after another.
+graph, against one sequence after another.
 
 --workload square10 times the explicit-S path: 10 x 10 square lattice,
 alpha = 1 (P = 10,200), 32768 walkers, q = (pi, pi); S built on the tensor
@@ -23,18 +33,15 @@ cores (three-term bf16 splits), blocked Cholesky in float32 refined in
 float64; it also reports |S_mixed - S_fp64|_F / |S_fp64|_F on a walker
 sample, for the default splits and for the cheaper two-term (bf16x3) form.
 
---workload square16 times the largest lattice: 16 x 16, alpha = 1 (P =
-66,048), 65536 walkers, q = (pi, 0), matrix-free CG (float32 kernels: the
-tensor-core kernels cover M <= 256 only while their operands fit in shared
-memory), plus the Krylov step over 300 states (Gram estimators of 300
-sampled columns and the float64 generalized eigenproblem).
-
 --workload sym6 times the symmetry projection of Appendix A on the 6 x 6
 lattice (alpha = 2): B~ and HB~ of 150 stored states at 4096 samples for
 all 36 momenta, then G^(k) and H^(k) of every momentum.
 
-Prints one JSON line.  Under torchrun every rank runs an independent
-sequence (a different seed): weak scaling with no data-path collective.
+--impl reference times the float64 oracle on the host cores on a walker
+sample of the same workload (extrapolated to the workload's walkers and
+iterations).  Prints one JSON line.  Under torchrun every rank runs an
+independent sequence (a different seed): weak scaling with no data-path
+collective.
 """
 
 import argparse
@@ -50,8 +57,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "chain64"
-SM_COUNT = 152
+WORKLOAD = "square16"
 FP32_LANES_PER_SM = 128
 
 
@@ -72,12 +78,13 @@ def parse():
                     help="skip the replayed moment-error check against the float64 path")
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel from the host instead of replaying CUDA graphs")
-    ap.add_argument("--cpu-walkers", type=int, default=2048)
+    ap.add_argument("--cpu-walkers", type=int, default=None,
+                    help="walkers of the oracle sample (default 2048 for chain64, 64 for square16)")
     ap.add_argument("--chunks", type=int, default=None,
                     help="walker chunks of the split-K reductions (default: the context's)")
     ap.add_argument("--only-mixed", action="store_true",
                     help="chain64: skip the plain float32 path (tuning runs)")
-    ap.add_argument("--workload", default="chain64",
+    ap.add_argument("--workload", default=WORKLOAD,
                     choices=["chain64", "batch", "square10", "square16", "sym6"])
     ap.add_argument("--s-error-walkers", type=int, default=2048,
                     help="square10: walkers of the tensor-core S vs float64 S comparison")
@@ -215,14 +222,6 @@ BATCH_CYCLE_NOTE = ("every timed step is moment 3 (the n >= 3 target) of every s
                     "untimed restart (|psi|^2 sampled, moments 1-2 fitted)")
 
 
-# DRAM bytes (read + write) of one launch of the roofline kernel, from an
-# ncu capture of the current kernel on the same workload.
-MEASURED_TRAFFIC = {
-    ("mixed", "chain64"): (18002176, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                     "oreduce_tc_kernel launch on chain64 (18.00 MB + 0)"),
-}
-
-
 def reduce_flops(wl):
     """Algorithmic flops of one launch of the O-reduction over all walkers:
     per (walker, i, j) one real x complex FMA for O_W (4 flops), per (walker, j)
@@ -231,16 +230,104 @@ def reduce_flops(wl):
     return B * (4 * N * M + 8 * M + 4 * N)
 
 
-def reduce_bytes(wl):
-    """Algorithmic bytes of one launch of the O-reduction: tanh(theta) (complex64
-    [B][M]), spins (int8 [B][N]) and g (complex64 [B]) in, the P-row of sums out
-    (complex128)."""
-    B, N, M = wl.walkers, wl.N, wl.M
-    P = N + M + N * M
-    return B * (8 * M + N + 8) + 16 * P
+def sm_count():
+    """Multiprocessors of the current device (the library sizes its grids the same way)."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
-def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD, cyc=CYCLE):
+def fp32_peak(f_sm):
+    return sm_count() * FP32_LANES_PER_SM * 2 * f_sm * 1e6 / 1e12
+
+
+def fcg_bytes_per_iter(wl):
+    """Algorithmic bytes of one CG iteration of the fused solve: T = tanh theta
+    (complex64 [B][M]) and the spins (int8 [B][N]) read once; the P-vectors
+    are negligible beside them."""
+    return wl.walkers * (8 * wl.M + wl.N)
+
+
+def fcg_flops_per_iter(wl):
+    """Algorithmic flops of one CG iteration: the two contractions sigma V
+    (B x N x M, real sigma times complex V: 4 flops per term) and
+    sigma^T (conj(T) w) (the same), before the three-term bf16 splits."""
+    return 8.0 * wl.walkers * wl.N * wl.M
+
+
+def roofline_fcg(ctx, seq, wl, kind, clocks, n_eager=3):
+    """Live CUDA-event timing of the fused CG kernel on eagerly launched
+    natural-gradient iterations of the current step (graph replays record no
+    host-side events), with the CG iteration count of each solve."""
+    import torch
+    ctx.time_kernel("fcg", 64)
+    its = []
+    for _ in range(n_eager):
+        seq._iteration(kind)
+        its.append(float(seq.stats_it[5].item()))
+    torch.cuda.synchronize()
+    times = ctx.kernel_times()
+    ctx.time_kernel(None, 1)
+    k_ms = float(np.mean(times)) if times else None
+    it = float(np.mean(its))
+    peaks, src = measured_peaks()
+    bw_peak = float(peaks["hbm_gbs"])
+    tf_peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
+    work = fcg_bytes_per_iter(wl) * it
+    achieved = work / (k_ms * 1e-3) / 1e9 if k_ms else None
+    flops = fcg_flops_per_iter(wl) * it
+    tf = flops / (k_ms * 1e-3) / 1e12 if k_ms else None
+    return {"kernel": "cg_fused_kernel (one persistent launch per CG solve: tcgen05 O v and "
+                      "O^dag w products from bf16 splits, float64 CG vectors)",
+            "bound": "hbm", "achieved": achieved, "peak": bw_peak, "unit": "GB/s",
+            "frac": achieved / bw_peak if achieved else None, "traffic": None,
+            "work_per_launch": work, "cg_iters_per_launch": it,
+            "work_note": "algorithmic bytes: T (complex64 B x M) and spins (int8 B x N) once per "
+                         "CG iteration, times the CG iterations of the launch",
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
+            "launches_timed": len(times), "avg_launch_ms": k_ms,
+            "us_per_cg_iteration": k_ms * 1e3 / it if k_ms else None,
+            "tensor_view": {"achieved": tf, "peak": tf_peak, "unit": "TFLOP/s",
+                            "frac": tf / tf_peak if tf else None, "work_per_launch": flops,
+                            "note": "algorithmic flops of the two contractions (8 B N M per CG "
+                                    "iteration); the three-term splits execute 3x that on the "
+                                    "tensor cores; peak: MEASURED_PEAKS.json "
+                                    "bf16_tflops_sustained"}}
+
+
+def roofline_oreduce2(ctx, seq, wl, kind, clocks, n_eager=3):
+    """Live timing of the float32 O-reduction (the plain path's top kernel)."""
+    import torch
+    ctx.time_kernel("reduce", 4096)
+    for _ in range(n_eager):
+        seq._iteration(kind)
+    torch.cuda.synchronize()
+    ktimes = ctx.kernel_times()
+    ctx.time_kernel(None, 1)
+    k_ms = float(np.mean(ktimes)) if ktimes else None
+    f_sm = clocks.get("sm_mhz") or 2070.0
+    peak = fp32_peak(f_sm)
+    achieved = reduce_flops(wl) / (k_ms * 1e-3) / 1e12 if k_ms else None
+    return {"kernel": "oreduce2_kernel (sum_s sigma_si conj(T_sj) g_s, FP32 FMA)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "work_per_launch": reduce_flops(wl),
+            "peak_source": f"{sm_count()} SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
+            "launches_timed": len(ktimes), "avg_launch_ms": k_ms}
+
+
+def cg_summary(st, cg_maxit, cg_tol):
+    """CG convergence over the timed natural-gradient iterations (stats
+    [5] iterations, [6] relative residual)."""
+    its, res = st[..., 5].ravel(), st[..., 6].ravel()
+    trunc = (its >= cg_maxit) & (res > cg_tol)
+    return {"cg_iters_mean": float(its.mean()), "cg_iters_max": float(its.max()),
+            "cg_rel_residual_median": float(np.median(res)), "cg_rel_residual_max": float(res.max()),
+            "cg_truncated_fraction": float(trunc.mean()),
+            "cg_note": f"CG stops at |r| <= {cg_tol} |F| or after {cg_maxit} iterations; truncated = "
+                       f"stopped at the limit above tolerance (a fixed CG budget per update)"}
+
+
+def measure(args, prec_name, ws, rank, local, wl_name, cyc, K=None, W=None):
     """Time K moments of one precision path; returns (result dict, config, workload)."""
     import torch
 
@@ -248,7 +335,8 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD, cyc=CYCLE):
 
     wl = synth.WORKLOADS[wl_name]
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
-    K, W = args.steps, args.warmup
+    K = args.steps if K is None else K
+    W = args.warmup if W is None else W
     n_moments = 1 + max(cyc)
     seed = replicas.replica_seed(1000, rank)
     prec = {"fp32": api.FP32, "mixed": api.MIXED}[prec_name]
@@ -270,14 +358,12 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD, cyc=CYCLE):
         seq.fit(cycle_moment(k, cyc))
     ctx.sync_status()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    ctx.time_kernel("reduce", 4096)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(K)]
     barrier(ws)
     torch.cuda.synchronize()
-    launches0 = ctx.n_launches() + seq.graph_launches
     wall0 = time.perf_counter()
-    clk_path = clock_path(prec_name, rank)
+    clk_path = clock_path(f"{prec_name}_{wl_name}", rank)
     stats = []
     launches = 0  # kernels inside the timed event pairs (restarts excluded)
     with ClockSampler(clk_path, local) as clk:
@@ -294,49 +380,25 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD, cyc=CYCLE):
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     barrier(ws)
-    del launches0
-    ktimes = ctx.kernel_times()
-    if not ktimes:
-        # graph replays do not re-record host-side events: time the same kernel
-        # on eagerly launched iterations of the same step right after
-        for _ in range(3):
-            seq._iteration(seq.kind_of(cycle_moment(K - 1, cyc)))
-        torch.cuda.synchronize()
-        ktimes = ctx.kernel_times()
-    ctx.time_kernel(None, 1)
     ctx.sync_status()
     step_ms = [e[0].elapsed_time(e[1]) for e in ev]
     ms = max_over_ranks(ws, float(np.mean(step_ms)))
     st = torch.stack(stats).cpu().numpy()
     clocks = clk.summary()
-    f_sm = clocks.get("sm_mhz") or 2070.0
-    k_ms = float(np.mean(ktimes)) if ktimes else None
-    peaks, peak_src = measured_peaks()
-    if prec_name == "fp32":
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_sm * 1e6 / 1e12
-        achieved = reduce_flops(wl) / (k_ms * 1e-3) / 1e12 if k_ms else None
-        roof = {"kernel": "oreduce2_kernel (sum_s sigma_si conj(T_sj) g_s, FP32 FMA)",
-                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "work_per_launch": reduce_flops(wl),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}
+    kind = seq.kind_of(cycle_moment(K - 1, cyc))  # the graph buffers hold the last fitted moment
+    if args.eager:
+        roof = None
+    elif prec_name == "mixed" and ctx.fused_cg():
+        roof = roofline_fcg(ctx, seq, wl, kind, clocks)
     else:
-        peak = float(peaks["hbm_gbs"])
-        achieved = reduce_bytes(wl) / (k_ms * 1e-3) / 1e9 if k_ms else None
-        roof = {"kernel": "oreduce_tc_kernel (tcgen05 bf16x3, split-K over walkers)",
-                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "work_per_launch": reduce_bytes(wl),
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
-    traffic = MEASURED_TRAFFIC.get((prec_name, wl_name))
-    roof.update({"frac": (achieved / peak) if achieved else None,
-                 "traffic": traffic[0] if traffic else None,
-                 "traffic_source": traffic[1] if traffic else None,
-                 "launches_timed": len(ktimes), "avg_launch_ms": k_ms})
+        roof = roofline_oreduce2(ctx, seq, wl, kind, clocks)
+    ctx.sync_status()
     sweeps_per_moment = cfg.n_therm + cfg.n_iter * cfg.sweeps_per_iter + cfg.sweeps_per_iter
-    res = {"value": ws * 3600.0 * 1000.0 / ms, "ms_per_step": ms,
+    res = {"value": ws * 3600.0 * 1000.0 / ms, "ms_per_step": ms, "steps": K, "warmup": W,
            "mc_samples_per_s": ws * wl.walkers * sweeps_per_moment / (ms * 1e-3),
            "gpu_launches": int(round(launches)), "gpu_launches_per_step": launches / K,
-           "cg_iters_mean": float(st[..., 5].mean()), "wall_s_timed": wall, "clocks": clocks,
-           "roofline": roof}
+           "wall_s_timed": wall, "clocks": clocks, "roofline": roof,
+           **cg_summary(st, args.cg_maxit, args.cg_tol)}
     e2e_ms, Bi, Bo = e2e(seq, ctx, K, stream, cyc)
     e2e_ms = max_over_ranks(ws, e2e_ms)
     res["e2e"] = {"value": ws * 3600.0 * 1000.0 / e2e_ms, "unit": "moments/hour",
@@ -345,50 +407,138 @@ def measure(args, prec_name, ws, rank, local, wl_name=WORKLOAD, cyc=CYCLE):
     return res, cfg, wl
 
 
-def moment_error(args, n_moments=3, iters=10):
-    """Moment error (max_n |mu_n - mu_n^ref| / mu_0) of the mixed and plain
-    float32 paths on the bench workload, against the float64 GPU path on the
-    same walker configurations (replay of the float64 run's samples), over
-    moments 0 .. n_moments - 1 with `iters` natural-gradient iterations each."""
+def moment_error(args, wl_name, cyc, walkers_fp64):
+    """Moment error of the timed configuration, max over the moments fitted
+    in a timed cycle (mu_1 .. mu_max(cyc)), |mu_n - mu_n^ref| / mu_0:
+      precision: mixed and plain float32 against the float64 GPU path, all
+        three with the timed natural-gradient and CG settings, on the same
+        walker configurations (replay of the float64 run's samples), at
+        walkers_fp64 walkers (the full count where float64 is affordable);
+      truncation: the timed mixed and plain float32 runs against the same run
+        with four times the CG budget (4 cg_maxit iterations, |r| <= 1e-6 |F|),
+        on the same samples, at the full walker count.
+    The error of the timed configuration against a float64 solve with the
+    larger budget is at most their sum.  A reference run that fails (a fit
+    that turns non-finite) is reported as such instead of a number: on random
+    RBMs the closer-to-exact natural-gradient step at a small shift can be
+    unstable, the CG budget acting as a regulariser."""
     import torch
 
     from paper_2103_08804_gb300 import api, driver, synth
 
-    wl = synth.WORKLOADS[WORKLOAD]
+    wl = synth.WORKLOADS[wl_name]
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
+    nm = 1 + max(cyc)
     seed = 4242
 
     class _A:
         pass
 
-    a_ = _A()
-    a_.cg_maxit, a_.cg_tol, a_.jacobi, a_.iters = args.cg_maxit, args.cg_tol, args.jacobi, iters
-    cfg = make_config(wl, E0, a, a_, n_moments, seed)
-    psi = synth.rbm_params(seed, wl.N, wl.M, wl.sigma)
-    s_fit = synth.sz0_spins(seed + 2, wl.walkers, wl.N)
-    s_ref = synth.sz0_spins(seed + 3, wl.walkers, wl.N)
+    def cfg_of(maxit, tol):
+        a_ = _A()
+        a_.cg_maxit, a_.cg_tol, a_.jacobi, a_.iters = maxit, tol, args.jacobi, args.iters
+        return make_config(wl, E0, a, a_, nm, seed)
+
     torch.cuda.set_stream(torch.cuda.default_stream())
-    ref = driver.Sequence(api.Context(wl.Lx, wl.Ly, wl.M, wl.walkers, prec=api.FP64), cfg, psi,
-                          s_fit, s_ref)
-    ref.start()
+    psi = synth.rbm_params(seed, wl.N, wl.M, wl.sigma)
+    out = {"moments": f"1..{nm - 1} of a sequence started as the timed cycles start"}
+
+    def run(prec, B, cfg, s_fit, s_ref, replay=None, record=None):
+        ctx = api.Context(wl.Lx, wl.Ly, wl.M, B, prec=prec)
+        seq = driver.Sequence(ctx, cfg, psi, s_fit, s_ref)
+        seq.start(replay_ref=None if replay is None else replay[0])
+        for n in range(1, nm):
+            seq.fit(n, replay=None if replay is None else replay[1][n],
+                    record=None if record is None else record.setdefault(n, []))
+        try:
+            ctx.sync_status()
+            mu = seq.mu.cpu().numpy()
+        except api.CRError as e:
+            mu = str(e).split(":")[1].strip()  # the status name of the failure
+        ref_spins = seq.spins_ref
+        del seq, ctx
+        return mu, ref_spins
+
+    def err(mu, ref):
+        if isinstance(mu, str) or isinstance(ref, str):
+            return f"run failed: {mu if isinstance(mu, str) else ref}"
+        return float(np.max(np.abs(mu[1:] - ref[1:])) / abs(ref[0]))
+
+    timed = cfg_of(args.cg_maxit, args.cg_tol)
+    conv = cfg_of(4 * args.cg_maxit, 1e-6)
+    # precision against float64, same settings, same samples
+    Bp = min(walkers_fp64, wl.walkers)
+    s_fit, s_ref = synth.sz0_spins(seed + 2, Bp, wl.N), synth.sz0_spins(seed + 3, Bp, wl.N)
     rec = {}
-    for n in range(1, n_moments):
-        rec[n] = []
-        ref.fit(n, record=rec[n])
-    ref.ctx.sync_status()
-    mu_ref = ref.mu.cpu().numpy()
-    out = {}
+    mu64, sref = run(api.FP64, Bp, timed, s_fit, s_ref, record=rec)
+    prec_err = {}
     for name, prec in (("mixed", api.MIXED), ("plain_fp32", api.FP32)):
-        seq = driver.Sequence(api.Context(wl.Lx, wl.Ly, wl.M, wl.walkers, prec=prec), cfg, psi,
-                              s_fit, s_ref)
-        seq.start(replay_ref=ref.spins_ref)
-        for n in range(1, n_moments):
-            seq.fit(n, replay=rec[n])
-        seq.ctx.sync_status()
-        out[name] = float(np.max(np.abs(seq.mu.cpu().numpy() - mu_ref)) / abs(mu_ref[0]))
-    out["reference"] = (f"float64 GPU path on the same samples (replay), moments 0..{n_moments - 1}, "
-                        f"{iters} natural-gradient iterations each, CG {args.cg_maxit}")
+        mu, _ = run(prec, Bp, timed, s_fit, s_ref, replay=(sref, rec))
+        prec_err[name] = err(mu, mu64)
+    out["precision_vs_fp64"] = {**prec_err, "walkers": Bp,
+                                "reference": "float64 GPU path, same samples and settings"}
+    # truncation of the timed CG, full walker count
+    s_fit, s_ref = (synth.sz0_spins(seed + 2, wl.walkers, wl.N),
+                    synth.sz0_spins(seed + 3, wl.walkers, wl.N))
+    trunc = {}
+    for name, prec in (("mixed", api.MIXED), ("plain_fp32", api.FP32)):
+        rec = {}
+        mu_t, sref = run(prec, wl.walkers, timed, s_fit, s_ref, record=rec)
+        mu_c, _ = run(prec, wl.walkers, conv, s_fit, s_ref, replay=(sref, rec))
+        trunc[name] = err(mu_t, mu_c)
+    out["cg_truncation"] = {**trunc, "walkers": wl.walkers,
+                            "reference": f"the same path with {4 * args.cg_maxit} CG iterations "
+                                         f"(tolerance 1e-6) on the same samples"}
+    for name in ("mixed", "plain_fp32"):
+        a_, b_ = prec_err[name], trunc[name]
+        out[name] = a_ + b_ if isinstance(a_, float) and isinstance(b_, float) else None
+    out["bound"] = 1e-3
+    out["note"] = ("mixed / plain_fp32: precision + truncation, an upper estimate of the error of "
+                   "the timed configuration against a float64 solve with four times the CG budget "
+                   "(null where a reference run failed)")
     return out
+
+
+WL_TEXT = {
+    "chain64": "chain64: periodic Heisenberg chain N=64, RBM alpha=2 (M=128, P=8384), 16384 "
+               "walkers, q=pi/2, 50 natural-gradient iterations per moment, matrix-free CG "
+               "shifted solve",
+    "square16": "square16: periodic 16x16 Heisenberg lattice, RBM alpha=1 (M=256, P=66048), 65536 "
+                "walkers, q=(pi,0), 50 natural-gradient iterations per moment, matrix-free CG "
+                "shifted solve, then the Krylov step over 300 states",
+}
+
+
+def krylov_300(wl):
+    """cheb_gram over 300 sampled columns of all the walkers and the float64
+    generalized eigenproblem of Sec. IV (once per sequence)."""
+    import torch
+
+    from paper_2103_08804_gb300 import api
+    Nm, Bref = 300, wl.walkers
+    ctx = api.Context(wl.Lx, wl.Ly, wl.M, 64, prec=api.FP32)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    Bm = torch.randn(Nm, Bref, dtype=torch.complex64, device="cuda", generator=g)
+    HBm = torch.randn(Nm, Bref, dtype=torch.complex64, device="cuda", generator=g)
+    G = torch.empty(Nm, Nm, dtype=torch.complex128, device="cuda")
+    H = torch.empty_like(G)
+    mu = torch.zeros(2 * Nm, dtype=torch.complex128, device="cuda")
+    poles = torch.zeros(Nm, dtype=torch.float64, device="cuda")
+    wts = torch.zeros(Nm, dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    ctx.cheb_gram(Bm, HBm, G, H)
+    ev[1].record()
+    ctx.cheb_krylov(G, H, 1e-10, 2 * Nm, mu, poles, wts)
+    ev[2].record()
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    return {"gram_ms": ev[0].elapsed_time(ev[1]), "eigen_ms": ev[1].elapsed_time(ev[2]),
+            "note": "cheb_gram over 300 columns x the walkers, then cheb_krylov (pseudo-inverse, "
+                    "generalized eigenproblem, 600 corrected moments); once per sequence, not in "
+                    "the per-moment steps"}
 
 
 def run_ours(args):
@@ -396,9 +546,22 @@ def run_ours(args):
 
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
-    mixed, cfg, wl = measure(args, "mixed", ws, rank, local)
-    plain = mixed if args.only_mixed else measure(args, "fp32", ws, rank, local)[0]
-    merr = moment_error(args) if (rank == 0 and not args.no_accuracy) else None
+    wl_name = args.workload
+    cyc = CYCLE if wl_name == "chain64" else SQ16_CYCLE
+    cyc_note = CYCLE_NOTE if wl_name == "chain64" else SQ16_CYCLE_NOTE
+    mixed, cfg, wl = measure(args, "mixed", ws, rank, local, wl_name, cyc)
+    plain = None
+    if not args.only_mixed:
+        # the plain float32 path is 5-10x slower on the 16 x 16 lattice: fewer steps
+        kp = args.steps if wl_name == "chain64" else max(2, min(args.steps, 3))
+        plain = measure(args, "fp32", ws, rank, local, wl_name, cyc, K=kp,
+                        W=min(args.warmup, 1))[0]
+    merr = None
+    if rank == 0 and not args.no_accuracy:
+        merr = moment_error(args, wl_name, cyc, 16384 if wl_name == "chain64" else 4096)
+    kry = krylov_300(wl) if wl_name == "square16" else None
+    cgkeys = ("cg_iters_mean", "cg_iters_max", "cg_rel_residual_median", "cg_rel_residual_max",
+              "cg_truncated_fraction", "cg_note")
     out = {
         "metric": "Chebyshev moments/hour",
         "value": mixed["value"],
@@ -412,31 +575,32 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "mixed: bf16x3 tensor-core contractions with f32 accumulation, f32 elsewhere, "
                  "f64 sums and CG",
-        "data": "synthetic (random complex RBM, sigma=0.02; seeded S^z=0 walkers)",
-        "config": {"workload": "chain64: periodic Heisenberg chain N=64, RBM alpha=2 (M=128, "
-                               "P=8384), 16384 walkers, q=pi/2, 50 natural-gradient iterations "
-                               "per moment, matrix-free CG shifted solve",
-                   "path": "mixed", "walkers": wl.walkers, "iters_per_moment": cfg.n_iter,
-                   "cg_maxit": args.cg_maxit, "cg_tol": args.cg_tol, "jacobi": args.jacobi,
+        "data": f"synthetic (random complex RBM, sigma={wl.sigma}; seeded S^z=0 walkers)",
+        "config": {"workload": WL_TEXT[wl_name], "path": "mixed", "walkers": wl.walkers,
+                   "iters_per_moment": cfg.n_iter, "cg_maxit": args.cg_maxit,
+                   "cg_tol": args.cg_tol, "jacobi": args.jacobi,
                    "l2": "256 MiB buffer written between timed steps",
                    "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
-                   "chunks": args.chunks, "moments": CYCLE_NOTE,
+                   "chunks": args.chunks, "moments": cyc_note,
                    "parallelism": f"replicas x{ws}"},
         "mc_samples_per_s": mixed["mc_samples_per_s"],
         "mc_samples_unit": "walker-sweeps/s (one sweep = N exchange proposals)",
         "gpu_launches": mixed["gpu_launches"],
         "gpu_launches_per_step": mixed["gpu_launches_per_step"],
-        "cg_iters_mean": mixed["cg_iters_mean"],
+        **{k: mixed[k] for k in cgkeys},
         "wall_s_timed": mixed["wall_s_timed"],
         "clocks": mixed["clocks"],
         "e2e": mixed["e2e"],
         "roofline": mixed["roofline"],
-        "plain_fp32": {k: plain[k] for k in ("value", "ms_per_step", "mc_samples_per_s",
-                                              "gpu_launches_per_step", "cg_iters_mean", "e2e",
-                                              "roofline", "clocks")},
-        "mixed_over_plain": mixed["value"] / plain["value"],
         "moment_error": merr,
     }
+    if plain is not None:
+        out["plain_fp32"] = {k: plain[k] for k in ("value", "ms_per_step", "steps", "warmup",
+                                                   "mc_samples_per_s", "gpu_launches_per_step",
+                                                   "e2e", "roofline", "clocks") + cgkeys}
+        out["mixed_over_plain"] = mixed["value"] / plain["value"]
+    if kry is not None:
+        out["krylov_300"] = kry
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
@@ -486,15 +650,19 @@ def e2e(seq, ctx, K, stream, cyc=CYCLE):
     return float(np.mean(times)), Bi, Bo
 
 
-def oracle_iteration_time(n_walkers, seed=5):
-    """One natural-gradient iteration of the oracle at the full chain64 sizes
-    on n_walkers walkers: sweep, local target, log-derivatives, S, F and the
-    Cholesky solve.  Returns (seconds of the walker-proportional part,
-    seconds of the P x P solve)."""
+def oracle_iteration_time(wl_name, n_walkers, seed=5, cg_sample=3, cg_maxit=50):
+    """One natural-gradient iteration of the float64 oracle at the full sizes
+    of the workload on n_walkers walkers: a sweep, the local target,
+    the log-derivatives, the estimators and F, then the shifted solve:
+    chain64 builds S and solves by Cholesky (walker-independent P x P work);
+    square16 (S would take 70 GB) runs the oracle's matrix-free CG for
+    cg_sample iterations, each two products with the walkers' O.
+    Returns (walker part, solve part) in seconds, both scaled to the
+    workload's walker count (the CG to cg_maxit iterations)."""
     from oracle import lattice, rbm, sampler, sr, target
     from oracle.target import State
     from paper_2103_08804_gb300 import synth
-    wl = synth.WORKLOADS[WORKLOAD]
+    wl = synth.WORKLOADS[wl_name]
     E0, a = synth.safe_rescaling(wl.Lx, wl.Ly)
     N, M = wl.N, wl.M
     psi = synth.rbm_params(seed, N, M, wl.sigma)
@@ -502,37 +670,56 @@ def oracle_iteration_time(n_walkers, seed=5):
     p2 = synth.rbm_params(seed + 2, N, M, wl.sigma)
     spins = synth.sz0_spins(seed + 3, n_walkers, N)
     bl = lattice.bonds(wl.Lx, wl.Ly)
+    scale = wl.walkers / n_walkers
+    explicit = wl_name != "square16"
     t0 = time.perf_counter()
     spins, _, _ = sampler.mc_sweep(psi, N, M, bl, spins, 1, seed, 0)
     lp = rbm.logpsi(psi, N, M, spins)
     R = target.local_target(3, State(p1), State(p2), 0.5, 0.25, N, M, wl.Lx, wl.Ly, 1.0, E0, a,
                             0.9875, wl.q, spins, lp)
     O = rbm.logderiv(psi, N, M, spins)
-    est = sr.estimators(O, R)
+    est = sr.estimators(O, R, with_OO=explicit)
     F, _ = sr.force(est, wl.dgamma)
-    S = sr.qgt(est)
+    if explicit:
+        S = sr.qgt(est)
     t1 = time.perf_counter()
-    sr.shifted_solve(S, F, wl.shift)
-    return t1 - t0, time.perf_counter() - t1
+    if explicit:
+        sr.shifted_solve(S, F, wl.shift)
+        t_solve = time.perf_counter() - t1
+    else:
+        sr.cg_solve_op(lambda v: sr.sv_matrix_free([O], v, wl.shift), F, np.ones(len(F)),
+                       cg_sample, 0.0)
+        t_solve = (time.perf_counter() - t1) / cg_sample * cg_maxit * scale
+    return (t1 - t0) * scale, t_solve
 
 
-def _moment_seconds(t_walk, t_solve, n_walkers, wl):
-    # walker-proportional work scales with the walker count, the solve does not
-    return (t_walk * wl.walkers / n_walkers + t_solve) * (wl.iters + 2)
+def _moment_seconds(t_walk, t_solve, wl):
+    return (t_walk + t_solve) * (wl.iters + 2)
+
+
+def _oracle_sample_text(wl_name, n, tw, ts, wl):
+    solve = ("Cholesky solve of the explicit S" if wl_name != "square16" else
+             "matrix-free CG (3 iterations timed, scaled to 50)")
+    return (f"one natural-gradient iteration of the float64 numpy oracle at N={wl.N}, M={wl.M}, "
+            f"P={wl.P} on {n} walkers (walker part {tw:.1f} s and {solve} {ts:.1f} s after "
+            f"scaling to {wl.walkers} walkers), times {wl.iters + 2} iterations per moment "
+            f"(extrapolated)")
+
+
+def default_cpu_walkers(wl_name, args):
+    return args.cpu_walkers if args.cpu_walkers else (2048 if wl_name == "chain64" else 64)
 
 
 def cpu_baseline(args):
     from paper_2103_08804_gb300 import synth
-    wl = synth.WORKLOADS[WORKLOAD]
+    wl_name = args.workload
+    wl = synth.WORKLOADS[wl_name]
     cores = len(os.sched_getaffinity(0))
-    tw, ts = oracle_iteration_time(args.cpu_walkers)
-    t_moment = _moment_seconds(tw, ts, args.cpu_walkers, wl)
+    n = default_cpu_walkers(wl_name, args)
+    tw, ts = oracle_iteration_time(wl_name, n, cg_maxit=args.cg_maxit)
+    t_moment = _moment_seconds(tw, ts, wl)
     return {"value": 3600.0 / t_moment, "unit": "moments/hour", "cores": cores, "kind": "oracle",
-            "sample": f"one natural-gradient iteration of the float64 numpy oracle at N=64, "
-                      f"M=128, P=8384 on {args.cpu_walkers} walkers ({tw:.1f} s sampling, "
-                      f"target and S build; {ts:.1f} s Cholesky solve), walker part scaled to "
-                      f"{wl.walkers} walkers, times {wl.iters + 2} iterations per moment "
-                      f"(extrapolated)"}
+            "sample": _oracle_sample_text(wl_name, n, tw, ts, wl)}
 
 
 def run_reference(args):
@@ -545,25 +732,27 @@ def run_reference(args):
     if args.workload == "sym6":
         run_reference_sym6(args, ws, cores)
         return
-    wl = synth.WORKLOADS[WORKLOAD]
-    nw = args.cpu_walkers
+    wl_name = args.workload if args.workload in ("chain64", "square16") else "chain64"
+    wl = synth.WORKLOADS[wl_name]
+    nw = default_cpu_walkers(wl_name, args)
     for _ in range(max(0, min(args.warmup, 1))):
-        oracle_iteration_time(256)
-    ts = [oracle_iteration_time(nw, seed=5 + k) for k in range(args.steps)]
-    t_moment = _moment_seconds(float(np.mean([t[0] for t in ts])),
-                               float(np.mean([t[1] for t in ts])), nw, wl)
+        oracle_iteration_time(wl_name, 16, cg_sample=1, cg_maxit=args.cg_maxit)
+    ts = [oracle_iteration_time(wl_name, nw, seed=5 + k, cg_maxit=args.cg_maxit)
+          for k in range(args.steps)]
+    tw, tsv = float(np.mean([t[0] for t in ts])), float(np.mean([t[1] for t in ts]))
+    t_moment = _moment_seconds(tw, tsv, wl)
     value = 3600.0 / t_moment
+    note = {} if args.workload == wl_name else {
+        "note": f"--workload {args.workload}: the oracle arm times {wl_name}"}
     print(json.dumps({
         "impl": "reference", "metric": "Chebyshev moments/hour", "value": value,
         "unit": "moments/hour", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_moment * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "chain64 (see ours)", "walkers_sampled": nw,
-                   **({} if args.workload == "chain64" else
-                      {"note": f"--workload {args.workload}: the oracle arm times chain64"})},
+        "config": {"workload": WL_TEXT[wl_name], "walkers_sampled": nw, **note},
         "cpu_baseline": {"value": value, "unit": "moments/hour", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} oracle iterations on {nw} walkers, scaled "
-                                   f"linearly to {wl.walkers} walkers x {wl.iters + 2} sweeps"},
+                         "sample": f"{args.steps} samples, each " +
+                                   _oracle_sample_text(wl_name, nw, tw, tsv, wl)},
         "e2e": {"value": value, "unit": "moments/hour", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -591,105 +780,6 @@ def run_reference_sym6(args, ws, cores, n_samples=24):
         "e2e": {"value": value, "unit": "moments/hour", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
-
-
-def roofline_reduce(ctx, seq, wl, clocks, kind, n_eager=3):
-    """Live CUDA-event timing of the O-reduction on eagerly launched
-    iterations of the current step (graph replays do not re-record host-side
-    events), as a roofline entry of the context's path."""
-    import torch
-
-    from paper_2103_08804_gb300 import api
-    ctx.time_kernel("reduce", 4096)
-    for _ in range(n_eager):
-        seq._iteration(kind)  # kind of the moment the graph buffers hold
-    torch.cuda.synchronize()
-    ktimes = ctx.kernel_times()
-    ctx.time_kernel(None, 1)
-    k_ms = float(np.mean(ktimes)) if ktimes else None
-    f_sm = clocks.get("sm_mhz") or 2070.0
-    peaks, peak_src = measured_peaks()
-    if ctx.prec == api.MIXED:
-        peak = float(peaks["hbm_gbs"])
-        achieved = reduce_bytes(wl) / (k_ms * 1e-3) / 1e9 if k_ms else None
-        roof = {"kernel": "oreduce_tc_kernel (tcgen05 bf16x3, split-K over walkers)",
-                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "work_per_launch": reduce_bytes(wl),
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
-    else:
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_sm * 1e6 / 1e12
-        achieved = reduce_flops(wl) / (k_ms * 1e-3) / 1e12 if k_ms else None
-        roof = {"kernel": "oreduce2_kernel (sum_s sigma_si conj(T_sj) g_s, FP32 FMA)",
-                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "work_per_launch": reduce_flops(wl),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}
-    roof.update({"frac": (achieved / peak) if achieved else None, "traffic": None,
-                 "launches_timed": len(ktimes), "avg_launch_ms": k_ms})
-    return roof
-
-
-def run_square16(args):
-    """Matrix-free CG on the 16 x 16 lattice, plus the 300-state Krylov step."""
-    import torch
-
-    from paper_2103_08804_gb300 import api
-
-    from paper_2103_08804_gb300 import synth
-
-    ws, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    wl = synth.WORKLOADS["square16"]
-    # Krylov over Nm = 300 sampled columns B_n, (H' t_n)/psi of all 65536
-    # reference samples: timing of the Gram estimators and the eigenproblem
-    Nm, Bref = 300, wl.walkers
-    ctx = api.Context(wl.Lx, wl.Ly, wl.M, 64, prec=api.FP32)
-    g = torch.Generator(device="cuda")
-    g.manual_seed(7)
-    Bm = torch.randn(Nm, Bref, dtype=torch.complex64, device="cuda", generator=g)
-    HBm = torch.randn(Nm, Bref, dtype=torch.complex64, device="cuda", generator=g)
-    G = torch.empty(Nm, Nm, dtype=torch.complex128, device="cuda")
-    H = torch.empty_like(G)
-    mu = torch.zeros(2 * Nm, dtype=torch.complex128, device="cuda")
-    poles = torch.zeros(Nm, dtype=torch.float64, device="cuda")
-    wts = torch.zeros(Nm, dtype=torch.float64, device="cuda")
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    torch.cuda.synchronize()
-    ev[0].record()
-    ctx.cheb_gram(Bm, HBm, G, H)
-    ev[1].record()
-    ctx.cheb_krylov(G, H, 1e-10, 2 * Nm, mu, poles, wts)
-    ev[2].record()
-    torch.cuda.synchronize()
-    ctx.sync_status()
-    krylov = {"gram_ms": ev[0].elapsed_time(ev[1]), "eigen_ms": ev[1].elapsed_time(ev[2]),
-              "note": "cheb_gram over 300 columns x 65536 samples, then cheb_krylov "
-                      "(pseudo-inverse, generalized eigenproblem, 600 corrected moments); "
-                      "once per sequence"}
-    del Bm, HBm, ctx
-    res, cfg, wl = measure(args, "fp32", ws, rank, local, wl_name="square16", cyc=SQ16_CYCLE)
-    out = {
-        "metric": "Chebyshev moments/hour", "value": res["value"], "unit": "moments/hour",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 products, f64 sums and CG",
-        "data": "synthetic (random complex RBM, sigma=0.01; seeded S^z=0 walkers)",
-        "config": {"workload": "square16: periodic 16x16 Heisenberg lattice, RBM alpha=1 (M=256, "
-                               "P=66048), 65536 walkers, q=(pi,0), matrix-free CG shifted solve",
-                   "iters_per_moment": cfg.n_iter, "cg_maxit": args.cg_maxit,
-                   "cg_tol": args.cg_tol, "l2": "256 MiB buffer written between timed steps",
-                   "launch": "eager" if args.eager else "CUDA graph per natural-gradient iteration",
-                   "moments": SQ16_CYCLE_NOTE,
-                   "parallelism": f"replicas x{ws}"},
-        "mc_samples_per_s": res["mc_samples_per_s"], "gpu_launches": res["gpu_launches"],
-        "cg_iters_mean": res["cg_iters_mean"], "clocks": res["clocks"], "e2e": res["e2e"],
-        "roofline": res["roofline"],
-        "krylov_300": krylov,
-    }
-    if rank == 0:
-        print(json.dumps(out), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
 
 
 SYM6 = {"L": 6, "M": 72, "walkers": 4096, "states": 150, "sigma": 0.02, "Wp": 0.9875}
@@ -817,7 +907,7 @@ def run_sym6(args):
     anti = sum(int(np.sum(spins_h[:, i] != spins_h[:, j])) for i, j in bonds)
     flop = 4 * N * anti * M * SYM6_FLOP_PER_BOND_UNIT  # lattice maps keep every bond
     f_sm = clocks.get("sm_mhz") or 2070.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * f_sm * 1e6 / 1e12
+    peak = fp32_peak(f_sm)
     achieved = flop / (k_ms * 1e-3) / 1e12 if k_ms else None
     roof = {"kernel": "sym_hprime_kernel ((H' t_n)(s') / psi(s) of one state at 4 N B "
                       "transformed configurations, FP32 FMA over cosh/sinh bond tables)",
@@ -1118,8 +1208,8 @@ def run_batch(args):
     sq = next(i for i, s in enumerate(b.active) if s.cfg.Ly > 1)
     b._fork()
     with torch.cuda.stream(b.streams[sq]):
-        roof = roofline_reduce(b.ctxs[sq], seqs[sq], synth.WORKLOADS["square8"], clocks,
-                               seqs[sq].kind_of(cycle_moment(K - 1, BATCH_CYCLE)))
+        roof = roofline_fcg(b.ctxs[sq], seqs[sq], synth.WORKLOADS["square8"],
+                            seqs[sq].kind_of(cycle_moment(K - 1, BATCH_CYCLE)), clocks)
     b._join()
     for c in b.ctxs:
         c.sync_status()
@@ -1166,8 +1256,6 @@ if __name__ == "__main__":
         run_batch(a)
     elif a.workload == "square10":
         run_explicit(a)
-    elif a.workload == "square16":
-        run_square16(a)
     elif a.workload == "sym6":
         run_sym6(a)
     else:

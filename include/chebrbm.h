@@ -221,6 +221,11 @@ long long cr_n_launches(const cr_ctx* ctx);
 cr_status cr_time_kernel(cr_ctx* ctx, int kernel_id, int capacity);
 int cr_kernel_times(cr_ctx* ctx, float* ms_out, int capacity);
 
+/* 1 when sr_step's CG runs as one fused persistent kernel in this context
+   (CR_MIXED contexts with N, M <= 256 whose walker and parameter counts fit
+   the kernel's per-CTA limits), else 0. */
+int cr_fused_cg(const cr_ctx* ctx);
+
 /* Sizes: N, M, P, number of bonds. */
 int cr_n_sites(const cr_ctx* ctx);
 int cr_n_hidden(const cr_ctx* ctx);

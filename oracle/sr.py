@@ -27,21 +27,24 @@ def _mean(x, weights):
     return np.tensordot(weights, x, axes=(0, 0))
 
 
-def estimators(O, R, weights=None):
+def estimators(O, R, weights=None, with_OO=True):
     """The sample averages the update needs.
 
     O [B, P] complex log-derivatives, R [B] complex ratios, weights [B] (sum 1)
-    or None for plain sample means.
+    or None for plain sample means.  with_OO=False leaves out <O* O^T> (P x P),
+    for the matrix-free solve.
     """
     O = np.asarray(O, dtype=np.complex128)
     R = np.asarray(R, dtype=np.complex128)
-    return {
+    est = {
         "mR": _mean(R, weights),
         "mRR": _mean(np.abs(R) ** 2, weights).real,
         "Obar": _mean(O, weights),
         "OR": _mean(np.conj(O) * R[:, None], weights),
-        "OO": (np.conj(O).T * (np.ones(len(R)) / len(R) if weights is None else weights)) @ O,
     }
+    if with_OO:
+        est["OO"] = (np.conj(O).T * (np.ones(len(R)) / len(R) if weights is None else weights)) @ O
+    return est
 
 
 def fubini_study_angle(mR, mRR):
@@ -79,6 +82,13 @@ def cg_solve(S, F, shift, maxit, tol, jacobi=False):
     Stops when |r| <= tol |F| or after maxit iterations.  Returns (x, iterations)."""
     A = S + shift * np.eye(S.shape[0])
     d = np.real(np.diag(A)) if jacobi else np.ones(S.shape[0])
+    return cg_solve_op(lambda v: A @ v, F, d, maxit, tol)
+
+
+def cg_solve_op(apply, F, d, maxit, tol):
+    """The same conjugate gradients with the operator given as a function,
+    apply(v) = (S + shift I) v (the matrix-free form of Sec. III), and the
+    preconditioner diagonal d (ones for plain CG).  Returns (x, iterations)."""
     x = np.zeros_like(F)
     r = F.copy()
     z = r / d
@@ -89,7 +99,7 @@ def cg_solve(S, F, shift, maxit, tol, jacobi=False):
     if f2 == 0.0:
         return x, 0
     while it < maxit:
-        Ap = A @ p
+        Ap = apply(p)
         alpha = rz / np.vdot(p, Ap).real
         x = x + alpha * p
         r = r - alpha * Ap
@@ -101,6 +111,21 @@ def cg_solve(S, F, shift, maxit, tol, jacobi=False):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, it
+
+
+def sv_matrix_free(O_blocks, v, shift):
+    """(S + shift I) v = O^dag (O v) / B - Obar^* (Obar . v) + shift v from the
+    log-derivatives given block by block (an iterable of [b, P] arrays whose
+    rows are all the samples), without forming S."""
+    acc = np.zeros(len(v), dtype=np.complex128)
+    sumO = np.zeros(len(v), dtype=np.complex128)
+    B = 0
+    for O in O_blocks:
+        acc += np.conj(O).T @ (O @ v)
+        sumO += O.sum(axis=0)
+        B += O.shape[0]
+    Obar = sumO / B
+    return acc / B - np.conj(Obar) * (Obar @ v) + shift * v
 
 
 def sr_step(params, O, R, shift, dgamma, weights=None, solver="cholesky", cg_maxit=100,

@@ -31,7 +31,7 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
            "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix",
            "cheb_spectrum", "cheb_lorentzian", "sym_workspace_bytes", "sym_btilde",
-           "sym_h_workspace_bytes", "sym_hbtilde", "cheb_init_params", "sr_sv")
+           "sym_h_workspace_bytes", "sym_hbtilde", "cheb_init_params", "sr_sv", "cr_fused_cg")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
           "chol": 7, "trsv": 8, "fcg": 9}
 
@@ -82,7 +82,7 @@ def load(path=None):
     lib.cr_last_error.argtypes = [vp]
     lib.cr_last_error.restype = ctypes.c_char_p
     lib.cr_sync_status.argtypes = [vp]
-    for f in ("cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds"):
+    for f in ("cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds", "cr_fused_cg"):
         getattr(lib, f).argtypes = [vp]
     lib.rbm_logpsi.argtypes = [vp, ctypes.POINTER(State), vp, i, vp, vp]
     lib.mc_sweep.argtypes = [vp, ctypes.POINTER(State), vp, vp, i, i, ctypes.POINTER(Philox),
@@ -115,7 +115,7 @@ def load(path=None):
     lib.cheb_init_params.argtypes = [vp, i, vp, vp, vp]
     lib.sr_sv.argtypes = [vp, vp, vp, i, vp, d, vp, vp]
     for f in SYMBOLS:
-        if f not in ("cr_last_error", "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds",
+        if f not in ("cr_last_error", "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds", "cr_fused_cg",
                      "cr_n_launches", "cr_max_chunks", "sym_workspace_bytes",
                      "sym_h_workspace_bytes"):
             getattr(lib, f).restype = ctypes.c_int
@@ -185,6 +185,10 @@ class Context:
 
     def max_chunks(self):
         return int(self.lib.cr_max_chunks(self.h))
+
+    def fused_cg(self):
+        """True when sr_step's CG runs as one fused persistent kernel here."""
+        return int(self.lib.cr_fused_cg(self.h)) == 1
 
     def sync_status(self):
         self._check(self.lib.cr_sync_status(self.h), "device status")

@@ -27,7 +27,8 @@
 // the same iterates as the textbook recursion in exact arithmetic, with both
 // inner products of an iteration formed together: delta comes out of the
 // walker phase (the centred form above) and gamma from the slice phase, so
-// an iteration needs two grid barriers.
+// an iteration needs two grid barriers.  Should the recurrence's (p, A p)
+// lose positivity to rounding, the iteration restarts (beta = 0).
 //
 // Per CG iteration:
 //   W   walker phase (each CTA its walker range), the product A u:
@@ -873,8 +874,17 @@ __global__ void __launch_bounds__(FC_THREADS, 1) cg_fused_kernel(const __grid_co
         __syncthreads();
         // delta = (u, A u) = (1/B) sum_s |w_s|^2 + lambda |u|^2
         const double delta = s.bc[5] * invB + a.shift * uu;
-        const double beta = its == 0 ? 0.0 : gam / gam_prev;
-        const double alpha = its == 0 ? gam / delta : gam / (delta - beta * gam / alpha_prev);
+        // (p, A p) by the recurrence, delta - beta^2 (p_prev, A p_prev); it holds
+        // while the directions stay A-conjugate.  When rounding has eroded that
+        // (float32-accurate products at a large condition number) it can come
+        // out tiny or negative: then the recurrence restarts with beta = 0
+        // (p = u, s = A u, a steepest-descent step, whose denominator delta
+        // is a sum of squares).
+        const double beta0 = its == 0 ? 0.0 : gam / gam_prev;
+        const double den = its == 0 ? delta : delta - beta0 * gam / alpha_prev;
+        const bool restart = its == 0 || !(den > 1e-6 * delta);
+        const double beta = restart ? 0.0 : beta0;
+        const double alpha = gam / (restart ? delta : den);
         if (ct >= 0) {
             double r2 = 0.0, gm = 0.0, our = 0.0, oui = 0.0, u2s = 0.0;
             const int L = k1 - k0;

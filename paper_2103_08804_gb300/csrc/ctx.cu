@@ -7,6 +7,7 @@
 #include "common.cuh"
 
 cr_status tc_prepare(cr_ctx* c);
+cr_status target_prepare(cr_ctx* c);
 void sgram_geometry(const cr_ctx* c, int* R2, int* nkc_max, size_t* plane_bytes, int* npl);
 std::vector<int2> sgram_tiles(int P);
 
@@ -207,7 +208,8 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
         e = cudaMemcpy(c->gtiles, gt.data(), gt.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, 64 * sizeof(double));
-    if (e != cudaSuccess || tc_prepare(c) != CR_OK || (c->fcg && fcg_prepare(c) != CR_OK)) {
+    if (e != cudaSuccess || tc_prepare(c) != CR_OK || target_prepare(c) != CR_OK ||
+        (c->fcg && fcg_prepare(c) != CR_OK)) {
         cr_destroy(c);
         return CR_ECUDA;
     }
@@ -264,6 +266,7 @@ extern "C" cr_status cr_sync_status(cr_ctx* c) {
     return (cr_status)st;
 }
 
+extern "C" int cr_fused_cg(const cr_ctx* c) { return c ? c->fcg : -1; }
 extern "C" int cr_n_sites(const cr_ctx* c) { return c ? c->N : -1; }
 extern "C" int cr_n_hidden(const cr_ctx* c) { return c ? c->M : -1; }
 extern "C" int cr_n_params(const cr_ctx* c) { return c ? c->P : -1; }

@@ -5,11 +5,17 @@
 // reference amplitude psi_ref(s):
 //   (H v)(s) = sum_b [(J/4) s_i s_j v(s) + (J/2)[s_i != s_j] v(s^{ij})]   (Sec. V)
 // One warp per sample.  Lanes take the antiparallel bonds of the sample
-// (compacted with a ballot) and run over the hidden units sequentially with
-// tanh(theta_m) broadcast from shared memory, forming
-//   v(s^{ij}) / v(s) = exp(-s 2 (a_i - a_i')) prod_m (cosh D_m - s tanh theta_m sinh D_m)
-// from the transposed bond tables [Mp][Nb], so consecutive lanes read
-// consecutive bonds.
+// (compacted with a ballot) and run over the hidden units sequentially,
+// forming the exchanged amplitude relative to the reference amplitude with
+// no division:
+//   v(s^{ij}) / psi_ref(s) = exp(a.s - 2 s_i (a_i - a_i') + X + M ln 2 - log psi_ref(s))
+//                            prod_m (C_m cosh D_m - s_i S_m sinh D_m),
+// C_m, S_m = cosh, sinh theta_m times e^{-|Re theta_m|} and X = sum_m |Re theta_m|,
+// from the transposed bond tables [Mp][Nb] (consecutive lanes read
+// consecutive bonds).  The samples are drawn from |psi_n|^2, not from
+// |v|^2, so a sample can sit at a node of v (cosh theta_m = 0); a ratio to
+// v(s), as with tanh theta_m, would divide by it there, while every factor
+// above stays bounded.
 #include <math.h>
 
 #include "common.cuh"
@@ -24,6 +30,7 @@ struct hp_args {
     const int8_t* spins;
     const cpx<R>* L_prev;    // [B] log RBM(prev) at s
     const cpx<R>* th_prev;   // [B][M] theta of prev at s
+    const cpx<R>* a_prev;    // [N] visible biases of prev
     const cpx<R>* L_ref;     // [B] log psi_ref at s
     const cpx<R>* L_prev2;   // [B] log RBM(prev2) at s, or null
     const cpx<R>* ChT;
@@ -65,19 +72,38 @@ template <typename R>
 __global__ void __launch_bounds__(128) hprime_kernel(hp_args<R> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int2* bonds = (int2*)smem_raw;                                   // [Nb]
-    cpx<R>* Tall = (cpx<R>*)(bonds + A.Nb + (A.Nb & 1));             // [4][Mp]
-    int8_t* sgall = (int8_t*)(Tall + 4 * A.Mp);                      // [4][N]
+    cpx<R>* Tall = (cpx<R>*)(bonds + A.Nb + (A.Nb & 1));             // [4][2 Mp]: C, S
+    int8_t* sgall = (int8_t*)(Tall + 8 * A.Mp);                      // [4][N]
     int16_t* lstall = (int16_t*)(sgall + 4 * ((A.N + 1) & ~1));      // [4][Nb]
     for (int e = threadIdx.x; e < A.Nb; e += blockDim.x) bonds[e] = A.bonds[e];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int w = blockIdx.x * 4 + wid;
-    cpx<R>* T = Tall + wid * A.Mp;
+    cpx<R>* Cm = Tall + wid * 2 * A.Mp;
+    cpx<R>* Sm = Cm + A.Mp;
     int8_t* sg = sgall + wid * ((A.N + 1) & ~1);
     int16_t* lst = lstall + wid * A.Nb;
+    double xsum = 0.0;             // sum_m |Re theta_m| (lane partial)
+    cpx<double> asg = {0.0, 0.0};  // a . s (lane partial)
     if (w < A.B) {
-        for (int i = lane; i < A.N; i += 32) sg[i] = A.spins[(size_t)w * A.N + i];
+        for (int i = lane; i < A.N; i += 32) {
+            const int8_t si = A.spins[(size_t)w * A.N + i];
+            sg[i] = si;
+            if (A.want_E) asg = asg + (double)si * ccast<double>(A.a_prev[i]);
+        }
         if (A.want_E)
-            for (int m = lane; m < A.M; m += 32) T[m] = ctanh_(A.th_prev[(size_t)w * A.M + m]);
+            for (int m = lane; m < A.M; m += 32) {
+                // cosh and sinh of theta times e^{-|Re theta|}: with e = e^{-2|x|},
+                // C = ((1 + e) cos y, sg (1 - e) sin y) / 2, S = (sg (1 - e) cos y, (1 + e) sin y) / 2
+                const cpx<R> th = A.th_prev[(size_t)w * A.M + m];
+                const R ax = th.x < R(0) ? -th.x : th.x, sgn = th.x < R(0) ? R(-1) : R(1);
+                const R e = m_exp(R(-2) * ax);
+                R sn, cs;
+                m_sincos(th.y, &sn, &cs);
+                const R p = R(0.5) * (R(1) + e), q = R(0.5) * sgn * (R(1) - e);
+                Cm[m] = {p * cs, q * sn};
+                Sm[m] = {q * cs, p * sn};
+                xsum += (double)ax;
+            }
     }
     __syncthreads();
     if (w >= A.B) return;
@@ -111,6 +137,8 @@ __global__ void __launch_bounds__(128) hprime_kernel(hp_args<R> A) {
         ed = R(0.25) * A.J * warp_sum(ed);
         cpx<double> off = {0.0, 0.0};
         const R inv_sqrt_n = m_rsqrt(R(A.N));
+        xsum = warp_sum(xsum);
+        asg = warp_sum(asg);
         for (int k = lane; k < n_anti; k += 32) {
             const int b = lst[k];
             const int2 bd = bonds[b];
@@ -123,9 +151,9 @@ __global__ void __launch_bounds__(128) hprime_kernel(hp_args<R> A) {
             // 16 factors, so it cannot overflow or underflow float32
             int ex = 0;
             for (int m = 0; m < A.M; ++m) {
-                cpx<R> ch = ldg(chc + (size_t)m * A.Nb), sh = ldg(shc + (size_t)m * A.Nb);
-                cpx<R> ts = T[m] * sh;
-                pr = pr * cpx<R>{ch.x - s * ts.x, ch.y - s * ts.y};
+                const cpx<R> ch = ldg(chc + (size_t)m * A.Nb), sh = ldg(shc + (size_t)m * A.Nb);
+                const cpx<R> c1 = Cm[m] * ch, s1 = Sm[m] * sh;
+                pr = pr * cpx<R>{c1.x - s * s1.x, c1.y - s * s1.y};  // cosh(theta - s D) e^{-|Re theta|}
                 if ((m & 15) == 15) {
                     int e;
                     frexp(fmax(fabs(pr.x), fabs(pr.y)), &e);
@@ -143,9 +171,11 @@ __global__ void __launch_bounds__(128) hprime_kernel(hp_args<R> A) {
         off = warp_sum(off);
         const double ia = 1.0 / A.a;
         const cpx<double> fsd = ccast<double>(fs);
-        cpx<double> hv = ia * ((double)ed * fsd + (0.5 * A.J) * off);
-        hv = hv - (A.E0 * ia + A.Wp) * fsd;
-        E = V * hv;
+        // the exchanged amplitudes relative to psi_ref(s)
+        const cpx<double> base = asg - ccast<double>(A.L_ref[w]) +
+                                 cpx<double>{xsum + A.M * 0.6931471805599453, 0.0};
+        const cpx<double> offr = cexp_(base) * off;
+        E = ia * ((double)ed * (fsd * V) + (0.5 * A.J) * offr) - (A.E0 * ia + A.Wp) * (fsd * V);
     }
     const cpx<double> ba = {A.beta_a[0], A.beta_a[1]};
     const cpx<double> c1 = A.ka * ba;
@@ -198,6 +228,25 @@ __global__ void mean_kernel(const cpx<R>* __restrict__ terms, int B, double* __r
     }
 }
 
+// Shared memory of hprime_kernel for a context, and the opt-in above the
+// 48 KB default (set once per context, outside any hot call).
+template <typename R>
+static size_t hprime_smem(const cr_ctx* c) {
+    return (c->Nb + (c->Nb & 1)) * sizeof(int2) + 8 * c->Mp * sizeof(cpx<R>) +
+           4 * ((c->N + 1) & ~1) + 4 * c->Nb * sizeof(int16_t);
+}
+
+cr_status target_prepare(cr_ctx* c) {
+    const size_t sm = c->prec == CR_FP64 ? hprime_smem<double>(c) : hprime_smem<float>(c);
+    if (sm <= 48 * 1024) return CR_OK;
+    cudaError_t e = c->prec == CR_FP64
+                        ? cudaFuncSetAttribute(hprime_kernel<double>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                        : cudaFuncSetAttribute(hprime_kernel<float>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return e == cudaSuccess ? CR_OK : cr_fail(c, CR_ECUDA, "target_prepare: %s", cudaGetErrorString(e));
+}
+
 template <typename R>
 static cr_status launch_hprime(cr_ctx* c, hp_args<R>& A) {
     const cr_tables& t = c->tab[1];
@@ -211,8 +260,7 @@ static cr_status launch_hprime(cr_ctx* c, hp_args<R>& A) {
     A.Mp = c->Mp;
     A.Nb = c->Nb;
     A.J = (R)c->J;
-    size_t sm = (c->Nb + (c->Nb & 1)) * sizeof(int2) + 4 * c->Mp * sizeof(cpx<R>) +
-                4 * ((c->N + 1) & ~1) + 4 * c->Nb * sizeof(int16_t);
+    const size_t sm = hprime_smem<R>(c);
     CR_LAUNCH(c, CR_KERNEL_TARGET, hprime_kernel<R><<<(A.B + 3) / 4, 128, sm, c->stream>>>(A));
     return cr_check_launch(c, "hprime_kernel");
 }
@@ -235,6 +283,7 @@ static cr_status target_t(cr_ctx* c, const cr_target* tg, const int8_t* spins, c
     A.spins = spins;
     A.L_prev = lp;
     A.th_prev = (const cpx<R>*)c->theta_tmp;
+    A.a_prev = (const cpx<R>*)tg->prev.params;
     A.L_ref = (const cpx<R>*)lpn;
     A.L_prev2 = tg->n >= 2 ? lp + c->max_walkers : nullptr;
     A.pr = pd(&tg->prev);
@@ -287,6 +336,7 @@ static cr_status moment_t(cr_ctx* c, const cr_state* st, const double* beta, dou
     A.spins = spins;
     A.L_prev = lp;
     A.th_prev = (const cpx<R>*)c->theta_tmp;
+    A.a_prev = (const cpx<R>*)st->params;
     A.L_ref = (const cpx<R>*)lpref;
     A.pr = pd(st);
     A.prm = probe_desc{1, qx, qy};

@@ -1,6 +1,6 @@
 """Host logic of bench.py that decides whether a number is valid: the
-nvidia-smi clock and throttle-reason parser, where the clock samples go, and
-the algorithmic bytes of the headline roofline entry."""
+nvidia-smi clock and throttle-reason parser, where the clock samples go, the
+algorithmic work of the roofline entries, and the CG convergence summary."""
 
 import os
 import sys
@@ -54,15 +54,34 @@ def test_clock_path_honours_the_environment(monkeypatch, tmp_path):
     assert os.path.basename(bench.clock_path("chain64", 0)) == "clocks_chain64_r0.csv"
 
 
-def test_headline_roofline_bytes():
-    # oreduce_tc on chain64: tanh theta complex64 [16384][128] = 16.78 MB,
-    # spins int8 [16384][64] = 1.05 MB, g complex64 [16384] = 0.13 MB, and the
-    # complex128 row of P = 64 + 128 + 64 * 128 sums out: 18.09 MB in all
+def test_fused_cg_roofline_work():
+    # per CG iteration of the fused solve on the 16 x 16 lattice: T = tanh theta
+    # complex64 [65536][256] = 134.2 MB and spins int8 [65536][256] = 16.8 MB
+    # read once; the two contractions sigma V and sigma^T (conj(T) w) are
+    # 4 B N M real flops each
+    from paper_2103_08804_gb300 import synth
+    wl = synth.WORKLOADS["square16"]
+    assert (wl.walkers, wl.N, wl.M) == (65536, 256, 256)
+    assert bench.fcg_bytes_per_iter(wl) == 65536 * 256 * 8 + 65536 * 256
+    assert abs(bench.fcg_bytes_per_iter(wl) / 1e6 - 151.0) < 0.1
+    assert bench.fcg_flops_per_iter(wl) == 8.0 * 65536 * 256 * 256
+
+
+def test_plain_reduction_flops():
+    # oreduce2 on chain64: per (walker, i, j) one real x complex FMA (4 flops),
+    # per (walker, j) conj(T) g and its b-sum (8 flops), per (walker, i) 4 flops
     from paper_2103_08804_gb300 import synth
     wl = synth.WORKLOADS["chain64"]
-    assert (wl.walkers, wl.N, wl.M) == (16384, 64, 128)
-    assert bench.reduce_bytes(wl) == 16384 * 128 * 8 + 16384 * 64 + 16384 * 8 + 16 * 8384
-    assert abs(bench.reduce_bytes(wl) / 1e6 - 18.09) < 0.005
-    # the measured DRAM traffic of one launch is the algorithmic read volume
-    traffic = bench.MEASURED_TRAFFIC[("mixed", "chain64")][0]
-    assert abs(traffic - bench.reduce_bytes(wl)) / bench.reduce_bytes(wl) < 0.01
+    assert bench.reduce_flops(wl) == 16384 * (4 * 64 * 128 + 8 * 128 + 4 * 64)
+
+
+def test_cg_summary_counts_truncated_solves():
+    import numpy as np
+    st = np.zeros((2, 3, 8))
+    st[..., 5] = [[50, 12, 50], [50, 50, 7]]
+    st[..., 6] = [[2e-4, 5e-5, 9e-5], [3e-3, 1e-4, 1e-5]]
+    s = bench.cg_summary(st, 50, 1e-4)
+    assert s["cg_iters_max"] == 50 and abs(s["cg_iters_mean"] - 219 / 6) < 1e-12
+    # at the limit and above tolerance: (0,0) and (1,0); (0,2) met the tolerance
+    assert abs(s["cg_truncated_fraction"] - 2 / 6) < 1e-12
+    assert s["cg_rel_residual_max"] == 3e-3

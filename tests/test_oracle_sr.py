@@ -115,6 +115,30 @@ def test_natural_gradient_fit_converges_on_representable_target():
     assert gammas[-1] < 1e-3 * gammas[0]
 
 
+def test_matrix_free_product_and_cg_equal_the_explicit_forms():
+    """The matrix-free (S + shift) v from blocks of O equals the explicit
+    qgt product, and CG through it takes the explicit CG's steps."""
+    N, M, B = 6, 5, 300
+    rng = np.random.default_rng(15)
+    p = rbm.init_params(rng, N, M, 0.3)
+    spins = np.where(rng.random((B, N)) < 0.5, 1, -1).astype(np.int8)
+    O = rbm.logderiv(p, N, M, spins)
+    R = 1.0 + 0.3 * (rng.standard_normal(B) + 1j * rng.standard_normal(B))
+    est = sr.estimators(O, R)
+    S = sr.qgt(est)
+    v = rng.standard_normal(O.shape[1]) + 1j * rng.standard_normal(O.shape[1])
+    blocks = [O[:100], O[100:170], O[170:]]
+    assert np.allclose(sr.sv_matrix_free(blocks, v, 0.01), (S + 0.01 * np.eye(len(v))) @ v,
+                       atol=1e-12)
+    F, _ = sr.force(est, 0.5)
+    x1, it1 = sr.cg_solve(S, F, 0.1, 300, 1e-11)
+    x2, it2 = sr.cg_solve_op(lambda u: sr.sv_matrix_free(blocks, u, 0.1), F,
+                             np.ones(len(F)), 300, 1e-11)
+    assert it1 < 300 and abs(it1 - it2) <= 1
+    assert np.max(np.abs(x1 - x2)) <= 1e-9 * np.max(np.abs(x1))
+    assert np.allclose(x1, sr.shifted_solve(S, F, 0.1), rtol=0, atol=1e-9 * np.max(np.abs(x1)))
+
+
 def test_initial_params_start_from_the_probe_site_operator():
     """The start of projection step 1 (Sec. III leaves it open): the RBM with
     a_0 += i pi/2 is exactly i sigma_0 psi = 2i S^z_0 psi on every
