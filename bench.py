@@ -1124,17 +1124,15 @@ def run_batch(args):
     b = batch.Batch(specs, prec=api.MIXED, tune=True)
     tune_s = time.perf_counter() - t0
     n_seq = len(b.seqs)
-    # The tuned chunk counts are measured (on throwaway sequences) and
-    # reported, but the timed steps run every context at its largest chunk
-    # count: a different summation order changes the rounding of the fits,
-    # and the fit at q = (pi, pi) of the 8 x 8 lattice is unstable enough
-    # (gamma jumping to ~1 rad with |F| ~ 6 within a few iterations of
-    # moment 2) that some orders blow up while others recover.
+    n_seq_all = int(replicas.sum_over_ranks(ws, n_seq))
+    # The autotuner timed the batched iteration graph on throwaway sequences
+    # over the fused-CG CTA counts and the reduction chunk counts, and applied
+    # the fastest setting.
     tuned = {"chunks": dict(zip([s.name for s in b.active], b.chunks)),
-             "iteration_ms_largest_chunks": b.timings[("max",)],
+             "fcg_ctas": dict(zip([s.name for s in b.active], b.ctas)),
+             "iteration_ms_default": b.timings[("max",)],
              "iteration_ms_tuned": b.tuned_ms,
-             "speedup": b.timings[("max",)] / b.tuned_ms, "applied": False}
-    b.set_chunks([c.max_chunks() for c in b.ctxs])
+             "speedup": b.timings[("max",)] / b.tuned_ms, "applied": True}
 
     def brestart():
         b.start()

@@ -221,6 +221,14 @@ long long cr_n_launches(const cr_ctx* ctx);
 cr_status cr_time_kernel(cr_ctx* ctx, int kernel_id, int capacity);
 int cr_kernel_times(cr_ctx* ctx, float* ms_out, int capacity);
 
+/* CTAs of the fused CG kernel (its walker-block shape: walkers per CTA =
+   ceil(B / n_ctas)).  0 (the default) takes one CTA per SM; a smaller count
+   leaves SMs to other sequences' kernels running at the same time (the
+   batch autotuner's knob).  Clamped below to what the kernel's per-CTA
+   limits need (512 walkers and 512 parameters per CTA); CR_EINVAL above the
+   SM count or for a context without the fused CG. */
+cr_status cr_set_fcg_ctas(cr_ctx* ctx, int n_ctas);
+
 /* 1 when sr_step's CG runs as one fused persistent kernel in this context
    (CR_MIXED contexts with N, M <= 256 whose walker and parameter counts fit
    the kernel's per-CTA limits), else 0. */
@@ -413,6 +421,40 @@ cr_status cheb_spectrum(cr_ctx* ctx, const double* mu, int Nm, double a, double 
 cr_status cheb_lorentzian(cr_ctx* ctx, const double* poles, const double* weights, int K,
                           double a, double Wp, double eta, const double* omega, int n_omega,
                           double* A_out);
+
+/* One sequence's part of a batched run (cr_batch_run): its context and
+   device buffers, the target of the projection step being fitted and the
+   update options. */
+typedef struct {
+    cr_ctx* ctx;            /* the sequence's context; its stream runs the sequence */
+    void* params;           /* RBM_n being fitted, complex [P], in/out */
+    int8_t* spins;          /* fit walkers [B][N], in/out */
+    void* theta;            /* complex [B][M], in/out: theta of params at spins */
+    void* tanh_theta;       /* complex [B][M], out (workspace) */
+    void* logpsi;           /* complex [B], in/out: log psi_n at spins */
+    void* R;                /* complex [B], out (workspace) */
+    int B;
+    int n_sweeps;           /* Metropolis sweeps per natural-gradient iteration */
+    cr_target target;       /* the target of projection step n (Sec. III) */
+    cr_sr_opts opts;
+    cr_philox* rng;         /* host struct (device_counter for graph replays) */
+    double* stats;          /* device float64 [CR_STATS_LEN] of the last iteration, or NULL */
+} cr_seq_iter;
+
+/* Secs. III and V: n_iter natural-gradient iterations of n_seqs
+   independent Chebyshev sequences (probe momenta, lattices of different
+   sizes), each iteration per sequence
+     mc_sweep (n_sweeps sweeps, giving log psi_n and tanh theta),
+     cheb_local_target (R), sr_step (the update), rbm_logpsi (theta, log psi_n
+     of the updated RBM),
+   each sequence on its own context's stream: the work is forked from
+   `stream` (a cudaStream_t, NULL = legacy default) and joined back into it
+   through events the contexts own, the sequences' launches interleaved
+   iteration by iteration so that they run side by side.  Nothing is
+   exchanged between sequences.  The whole call can be captured into one
+   CUDA graph on `stream`.  The contexts must be distinct.  Returns the first
+   failing call's status (its text in that context's cr_last_error). */
+cr_status cr_batch_run(const cr_seq_iter* seqs, int n_seqs, int n_iter, void* stream);
 
 /* Sec. III: the explicit S + shift I of sr_step's Cholesky path, built by
    the same kernels on samples of |psi|^2 (Obar from the same samples), copied

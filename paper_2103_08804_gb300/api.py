@@ -31,7 +31,8 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
            "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix",
            "cheb_spectrum", "cheb_lorentzian", "sym_workspace_bytes", "sym_btilde",
-           "sym_h_workspace_bytes", "sym_hbtilde", "cheb_init_params", "sr_sv", "cr_fused_cg")
+           "sym_h_workspace_bytes", "sym_hbtilde", "cheb_init_params", "sr_sv", "cr_fused_cg",
+           "cr_set_fcg_ctas", "cr_batch_run")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
           "chol": 7, "trsv": 8, "fcg": 9}
 
@@ -61,6 +62,15 @@ class SROpts(ctypes.Structure):
                 ("solver", ctypes.c_int), ("cg_maxit", ctypes.c_int),
                 ("cg_tol", ctypes.c_double), ("cg_precond", ctypes.c_int), ("mode", ctypes.c_int),
                 ("cg_strict", ctypes.c_int)]
+
+
+class SeqIter(ctypes.Structure):
+    """cr_seq_iter: one sequence's part of a cr_batch_run call."""
+    _fields_ = [("ctx", ctypes.c_void_p), ("params", ctypes.c_void_p), ("spins", ctypes.c_void_p),
+                ("theta", ctypes.c_void_p), ("tanh_theta", ctypes.c_void_p),
+                ("logpsi", ctypes.c_void_p), ("R", ctypes.c_void_p), ("B", ctypes.c_int),
+                ("n_sweeps", ctypes.c_int), ("target", Target), ("opts", SROpts),
+                ("rng", ctypes.POINTER(Philox)), ("stats", ctypes.c_void_p)]
 
 
 _lib = None
@@ -114,6 +124,8 @@ def load(path=None):
     lib.logpsi_backward_noalloc.argtypes = [i, i, i, vp, vp, i, vp, vp, vp, ctypes.c_char_p, i]
     lib.cheb_init_params.argtypes = [vp, i, vp, vp, vp]
     lib.sr_sv.argtypes = [vp, vp, vp, i, vp, d, vp, vp]
+    lib.cr_set_fcg_ctas.argtypes = [vp, i]
+    lib.cr_batch_run.argtypes = [ctypes.POINTER(SeqIter), i, i, vp]
     for f in SYMBOLS:
         if f not in ("cr_last_error", "cr_n_sites", "cr_n_hidden", "cr_n_params", "cr_n_bonds", "cr_fused_cg",
                      "cr_n_launches", "cr_max_chunks", "sym_workspace_bytes",
@@ -189,6 +201,23 @@ class Context:
     def fused_cg(self):
         """True when sr_step's CG runs as one fused persistent kernel here."""
         return int(self.lib.cr_fused_cg(self.h)) == 1
+
+    def set_fcg_ctas(self, n_ctas):
+        """CTAs of the fused CG kernel (0: one per SM)."""
+        self._check(self.lib.cr_set_fcg_ctas(self.h, int(n_ctas)), "cr_set_fcg_ctas")
+
+    def target(self, n, prev, prev2, beta_prev, beta_prev2, E0, a, Wp):
+        """The cr_target of projection step n (prev / prev2: State structs,
+        beta_*: device complex128 scalars)."""
+        tg = Target()
+        tg.n = n
+        tg.prev = prev
+        if prev2 is not None:
+            tg.prev2 = prev2
+        tg.beta_prev = beta_prev.data_ptr()
+        tg.beta_prev2 = beta_prev2.data_ptr() if beta_prev2 is not None else None
+        tg.E0, tg.a, tg.Wp = E0, a, Wp
+        return tg
 
     def sync_status(self):
         self._check(self.lib.cr_sync_status(self.h), "device status")
@@ -268,14 +297,7 @@ class Context:
         for bt in (beta_prev, beta_prev2, mean_out):
             if bt is not None and not (bt.is_cuda and bt.dtype == torch.complex128):
                 raise ValueError("beta / mean_out: need CUDA complex128 scalars")
-        tg = Target()
-        tg.n = n
-        tg.prev = prev
-        if prev2 is not None:
-            tg.prev2 = prev2
-        tg.beta_prev = beta_prev.data_ptr()
-        tg.beta_prev2 = beta_prev2.data_ptr() if beta_prev2 is not None else None
-        tg.E0, tg.a, tg.Wp = E0, a, Wp
+        tg = self.target(n, prev, prev2, beta_prev, beta_prev2, E0, a, Wp)
         self._check(self.lib.cheb_local_target(self.h, ctypes.byref(tg), _ptr(spins),
                                                _ptr(logpsi_n), B, _ptr(R_out), _ptr(mean_out)),
                     "cheb_local_target")
@@ -452,3 +474,14 @@ class Context:
         self._check(self.lib.cheb_krylov(self.h, _ptr(G), _ptr(H), Nm, cutoff, n_out, _ptr(mu_out),
                                          _ptr(poles_out), _ptr(weights_out), _ptr(rank_out)),
                     "cheb_krylov")
+
+
+def batch_run(iters, n_iter, stream):
+    """cr_batch_run over a list of SeqIter structs (from Sequence.iter_desc);
+    stream: the torch stream to fork from and join into."""
+    lib = load()
+    arr = (SeqIter * len(iters))(*iters)
+    st = lib.cr_batch_run(arr, len(iters), int(n_iter), ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        msgs = {lib.cr_last_error(it.ctx).decode(errors="replace") for it in iters}
+        raise CRError(f"cr_batch_run: {STATUS.get(st, st)}: {'; '.join(m for m in msgs if m)}")

@@ -5,20 +5,24 @@ momentum q (Sec. II), and the sequences are independent: nothing is
 exchanged between them.  A Batch gives every sequence its own library
 context (its own workspace), its own CUDA stream and the fixed buffers of a
 graph-mode Sequence, and captures one natural-gradient iteration of ALL
-sequences into a single CUDA graph, each sequence on a forked stream.  One
-replay then launches every sequence's kernels at once, so small sequences
-that cannot fill the GPU alone run side by side.
+sequences into a single CUDA graph through one cr_batch_run call (the
+library forks every sequence onto its context's stream, interleaves their
+launches and joins them back).  One replay then launches every sequence's
+kernels at once, so small sequences that cannot fill the GPU alone run side
+by side.
 
 schedule="per_q" is the baseline: each sequence replays its own iteration
 graph, one sequence after another on one stream.
 
 Both schedules launch the same kernels with the same arguments on the same
-data, so they give bit-identical moments; only the overlap differs.  The
-one tuning knob is the number of walker chunks of each context's split-K
-reductions (cr_set_chunks): fewer chunks launch fewer CTAs per reduction,
-which pays when many sequences share the GPU.  The autotuner times the
-batched iteration graph on throwaway copies of the sequences, first with one
-chunk count for all, then per lattice group.
+data, so they give bit-identical moments; only the overlap differs.  Two
+knobs shape the kernels of a sequence that shares the GPU: the CTA count
+(walker-block shape) of its fused CG kernel (cr_set_fcg_ctas: fewer, wider
+blocks leave SMs to the other sequences' cooperative launches) and the
+walker chunks of its split-K reductions (cr_set_chunks).  The autotuner
+times the batched iteration graph on throwaway copies of the sequences,
+first the CTA counts, then the chunk counts, each for all sequences and
+then per lattice group, and applies the fastest setting.
 
 A sequence whose probe vanishes identically (q = 0 on the S^z = 0 sector,
 where f_q = 0 and R is undefined) is not run: its moments are zero.
@@ -66,6 +70,7 @@ class Batch:
     prec: int = api.FP32
     tune: bool = True
     chunk_candidates: tuple = (8, 16, 32, 64, 128)
+    cta_divisors: tuple = (1, 2, 4, 8)
     tune_reps: int = 5
     timings: dict = field(default_factory=dict)
 
@@ -78,7 +83,8 @@ class Batch:
         for s in self.active:
             st = torch.cuda.Stream()
             B = max(s.spins_fit.shape[0], s.spins_ref.shape[0])
-            ctx = api.Context(s.cfg.Lx, s.cfg.Ly, s.cfg.M, B, self.prec, J=s.cfg.J, stream=st)
+            ctx = api.Context(s.cfg.Lx, s.cfg.Ly, s.cfg.M, B, self.prec, J=s.cfg.J, stream=st,
+                              explicit_s=s.cfg.solver == api.SOLVE_CHOLESKY)
             with torch.cuda.stream(st):
                 seq = Sequence(ctx, s.cfg, s.psi, s.spins_fit, s.spins_ref, graphs=True)
             self.ctxs.append(ctx)
@@ -87,6 +93,7 @@ class Batch:
         torch.cuda.synchronize()
         self._graphs = {}
         self.chunks = [c.max_chunks() for c in self.ctxs]
+        self.ctas = [0] * len(self.ctxs)
         self.graph_launches = 0
         if self.tune:
             self.autotune()
@@ -108,6 +115,14 @@ class Batch:
         self.chunks = [c for c in chunks]
         self._graphs = {}
 
+    def set_ctas(self, ctas):
+        """CTA counts of the contexts' fused CG kernels (0: one per SM)."""
+        for ctx, n in zip(self.ctxs, ctas):
+            if ctx.fused_cg():
+                ctx.set_fcg_ctas(n)
+        self.ctas = list(ctas)
+        self._graphs = {}
+
     # -------------------------------------------------------------- graphs
     def _capture(self, seqs, kind):
         """One iteration of every sequence in seqs, each on its own stream,
@@ -118,16 +133,11 @@ class Batch:
         cap.wait_stream(main)
         self._fork()
         n0 = sum(c.n_launches() for c in self.ctxs)
-        with torch.cuda.graph(g, stream=cap):
-            for seq, st in zip(seqs, self.streams):
-                st.wait_stream(cap)
-                with torch.cuda.stream(st):
-                    seq.ctx.set_stream(st)
-                    seq._iteration(kind)
-            for st in self.streams[:len(seqs)]:
-                cap.wait_stream(st)
         for seq, st in zip(seqs, self.streams):
             seq.ctx.set_stream(st)
+        iters = [seq.iter_desc(kind) for seq in seqs]
+        with torch.cuda.graph(g, stream=cap):
+            api.batch_run(iters, 1, cap)
         main.wait_stream(cap)
         return g, sum(c.n_launches() for c in self.ctxs) - n0
 
@@ -162,9 +172,11 @@ class Batch:
         self._eager(seqs, 1)
         return seqs
 
-    def _time_graph(self, seqs, chunks):
-        for ctx, n in zip(self.ctxs, chunks):
+    def _time_graph(self, seqs, chunks, ctas):
+        for ctx, n, m in zip(self.ctxs, chunks, ctas):
             ctx.set_chunks(min(n, ctx.max_chunks()))
+            if ctx.fused_cg():
+                ctx.set_fcg_ctas(m)
         g, _ = self._capture(seqs, 1)
         for _ in range(2):
             g.replay()
@@ -177,33 +189,48 @@ class Batch:
         return e0.elapsed_time(e1) / self.tune_reps
 
     def autotune(self):
-        """Pick each context's chunk count by timing the batched iteration
-        graph on throwaway sequences (the real ones are not touched)."""
+        """Pick each context's fused-CG CTA count and reduction chunk count by
+        timing the batched iteration graph on throwaway sequences (the real
+        ones are not touched), then apply them."""
         seqs = self._throwaway()
-        best = list(self.chunks)
-        t_best = self._time_graph(seqs, best)
-        self.timings = {("max",): t_best}
-        for n in self.chunk_candidates:
-            cand = [min(n, c.max_chunks()) for c in self.ctxs]
-            t = self._time_graph(seqs, cand)
-            self.timings[("all", n)] = t
-            if t < t_best:
-                best, t_best = cand, t
+        n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         groups = {}
         for i, s in enumerate(self.active):
             groups.setdefault((s.cfg.Lx, s.cfg.Ly, s.cfg.M), []).append(i)
+        best_ch, best_ct = list(self.chunks), list(self.ctas)
+        t_best = self._time_graph(seqs, best_ch, best_ct)
+        self.timings = {("max",): t_best}
+
+        def trial(key, ch, ct):
+            nonlocal best_ch, best_ct, t_best
+            if (ch, ct) == (best_ch, best_ct):
+                return
+            t = self._time_graph(seqs, ch, ct)
+            self.timings[key] = t
+            if t < t_best:
+                best_ch, best_ct, t_best = ch, ct, t
+
+        # walker-block shape of the fused CG: n_sm / d CTAs per sequence
+        fcg = any(c.fused_cg() for c in self.ctxs)
+        for d in self.cta_divisors[1:] if fcg else ():
+            trial(("ctas", d), best_ch, [max(1, n_sm // d)] * len(self.ctxs))
+        if fcg and len(groups) > 1:
+            for key, idx in groups.items():
+                for d in self.cta_divisors:
+                    ct = list(best_ct)
+                    for i in idx:
+                        ct[i] = 0 if d == 1 else max(1, n_sm // d)
+                    trial(("ctas", key, d), best_ch, ct)
+        # walker chunks of the split-K reductions
+        for n in self.chunk_candidates:
+            trial(("all", n), [min(n, c.max_chunks()) for c in self.ctxs], best_ct)
         if len(groups) > 1:
             for key, idx in groups.items():
                 for n in self.chunk_candidates:
-                    cand = list(best)
+                    ch = list(best_ch)
                     for i in idx:
-                        cand[i] = min(n, self.ctxs[i].max_chunks())
-                    if cand == best:
-                        continue
-                    t = self._time_graph(seqs, cand)
-                    self.timings[(key, n)] = t
-                    if t < t_best:
-                        best, t_best = cand, t
+                        ch[i] = min(n, self.ctxs[i].max_chunks())
+                    trial((key, n), ch, best_ct)
         self.tuned_ms = t_best
         del seqs
         # the throwaway sequences replayed one iteration many times over; a
@@ -214,9 +241,10 @@ class Batch:
                 ctx.sync_status()
             except api.CRError:
                 pass
-        self.set_chunks(best)
+        self.set_chunks(best_ch)
+        self.set_ctas(best_ct)
         torch.cuda.synchronize()
-        return best
+        return best_ch, best_ct
 
     # -------------------------------------------------------------- driving
     def start(self):

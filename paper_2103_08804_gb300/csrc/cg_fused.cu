@@ -996,8 +996,11 @@ static bool fcg_geometry(const cr_ctx* c, int B, Geo* g) {
     g->P = c->P;
     g->B = B;
     int G = (B + 31) / 32;
+    if (c->fcg_ctas > 0 && c->fcg_ctas < G) G = c->fcg_ctas;  // the walker-block shape chosen
     const int Gp = (c->P + KS_MAX - 1) / KS_MAX;  // every CTA's CG slice fits in shared memory
+    const int Gw = (B + MAX_WPC - 1) / MAX_WPC;   // and its walkers
     if (G < Gp) G = Gp;
+    if (G < Gw) G = Gw;
     if (G > c->n_sm) G = c->n_sm;
     g->G = G;
     g->wpc = (B + G - 1) / G;

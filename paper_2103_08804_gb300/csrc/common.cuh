@@ -206,6 +206,8 @@ struct cr_ctx {
     void* fcg_part;          // partial rows, complex float32 [n_sm][P]
     double* fcg_psc;         // scalar partials [n_sm][8]
     unsigned* fcg_bar;       // grid-barrier counter and abort flag
+    int fcg_ctas;            // CTAs of the fused CG (0: one per SM)
+    cudaEvent_t ev_fork, ev_join;  // batched runs: fork from / join into the caller's stream
 };
 
 static inline int rsize(const cr_ctx* c) { return c->prec == CR_FP64 ? 8 : 4; }

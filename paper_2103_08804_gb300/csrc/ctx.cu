@@ -202,6 +202,11 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
         cr_destroy(c);
         return e == cudaErrorMemoryAllocation ? CR_ENOMEM : CR_ECUDA;
     }
+    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cr_destroy(c);
+        return CR_ECUDA;
+    }
     std::vector<int2> bonds = make_bonds(c->Lx, c->Ly);
     e = cudaMemcpy(c->d_bonds, bonds.data(), Nb * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !gt.empty())
@@ -220,6 +225,8 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
 extern "C" cr_status cr_destroy(cr_ctx* c) {
     if (!c) return CR_EINVAL;
     kt_free(c);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     void* ptrs[] = {c->d_status, c->d_bonds, c->theta_tmp, c->lp_tmp, c->u_tmp, c->partial,
                     c->red, c->F, c->cg, c->p_lo, c->cgpart, c->scal, c->S, c->O_tmp, c->kry,
                     c->Lf, c->Xt, c->gtiles, c->fcg_a1, c->fcg_b2, c->fcg_v2, c->fcg_vab,
@@ -267,6 +274,56 @@ extern "C" cr_status cr_sync_status(cr_ctx* c) {
 }
 
 extern "C" int cr_fused_cg(const cr_ctx* c) { return c ? c->fcg : -1; }
+
+extern "C" cr_status cr_set_fcg_ctas(cr_ctx* c, int n_ctas) {
+    if (!c) return CR_EINVAL;
+    if (!c->fcg) return cr_fail(c, CR_EINVAL, "cr_set_fcg_ctas: no fused CG in this context");
+    if (n_ctas < 0 || n_ctas > c->n_sm)
+        return cr_fail(c, CR_EINVAL, "cr_set_fcg_ctas: %d outside [0, %d]", n_ctas, c->n_sm);
+    c->fcg_ctas = n_ctas;
+    return CR_OK;
+}
+
+// One natural-gradient iteration of a sequence, on its context's stream.
+static cr_status seq_iteration(const cr_seq_iter* q) {
+    cr_ctx* c = q->ctx;
+    cr_state st = {q->params, 0, 0.0, 0.0};
+    cr_status s = mc_sweep(c, &st, q->spins, q->theta, q->B, q->n_sweeps, q->rng, q->logpsi,
+                           q->tanh_theta, nullptr);
+    if (s == CR_OK) s = cheb_local_target(c, &q->target, q->spins, q->logpsi, q->B, q->R, nullptr);
+    if (s == CR_OK) s = sr_step(c, q->params, q->spins, q->tanh_theta, q->R, q->B, &q->opts, q->stats);
+    if (s == CR_OK) s = rbm_logpsi(c, &st, q->spins, q->B, q->theta, q->logpsi);
+    return s;
+}
+
+extern "C" cr_status cr_batch_run(const cr_seq_iter* seqs, int n, int n_iter, void* stream) {
+    if (!seqs || n < 1 || n_iter < 0) return CR_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!seqs[i].ctx) return CR_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (seqs[j].ctx == seqs[i].ctx)
+                return cr_fail(seqs[i].ctx, CR_EINVAL, "cr_batch_run: a context appears twice");
+    }
+    cudaStream_t main = (cudaStream_t)stream;
+    for (int i = 0; i < n; ++i) {
+        cr_ctx* c = seqs[i].ctx;
+        if (cudaEventRecord(c->ev_fork, main) != cudaSuccess ||
+            cudaStreamWaitEvent(c->stream, c->ev_fork, 0) != cudaSuccess)
+            return cr_fail(c, CR_ECUDA, "cr_batch_run: fork");
+    }
+    cr_status st = CR_OK;
+    for (int it = 0; it < n_iter && st == CR_OK; ++it)
+        for (int i = 0; i < n && st == CR_OK; ++i) st = seq_iteration(&seqs[i]);
+    // join every stream, also after a failure, so that the caller's stream
+    // orders after whatever was enqueued
+    for (int i = 0; i < n; ++i) {
+        cr_ctx* c = seqs[i].ctx;
+        if (cudaEventRecord(c->ev_join, c->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(main, c->ev_join, 0) != cudaSuccess)
+            return cr_fail(c, CR_ECUDA, "cr_batch_run: join");
+    }
+    return st;
+}
 extern "C" int cr_n_sites(const cr_ctx* c) { return c ? c->N : -1; }
 extern "C" int cr_n_hidden(const cr_ctx* c) { return c ? c->M : -1; }
 extern "C" int cr_n_params(const cr_ctx* c) { return c ? c->P : -1; }

@@ -17,6 +17,7 @@ RBM_1 starts from psi with a_0 += i pi/2 (exactly proportional to
 S^z_0 psi); RBM_n (n >= 2) starts from RBM_{n-1} (cheb_init_params).
 """
 
+import ctypes
 from dataclasses import dataclass
 
 import numpy as np
@@ -201,6 +202,25 @@ class Sequence:
                   solver=cfg.solver, cg_maxit=cfg.cg_maxit, cg_tol=cfg.cg_tol,
                   stats_out=self.stats_it, jacobi=cfg.jacobi)
         c.rbm_logpsi(self.work, self.spins, self.theta, self.lp)
+
+    def iter_desc(self, kind):
+        """The cr_seq_iter of one natural-gradient iteration on the fixed
+        buffers (graph mode), for cr_batch_run; the structs it points to are
+        kept alive on the sequence."""
+        c, cfg, q = self.ctx, self.cfg, self.cfg.q
+        prev = c.state(self.prev_buf, probe=(kind == 1), q=q)
+        prev2 = c.state(self.prev2_buf, probe=(kind == 2), q=q) if kind >= 2 else None
+        tg = c.target(1 if kind == 1 else 2, prev, prev2, self.beta_buf[0:1],
+                      self.beta_buf[1:2] if kind >= 2 else None, cfg.E0, cfg.a, cfg.Wp)
+        o = api.SROpts(cfg.dgamma, cfg.shift, cfg.solver, cfg.cg_maxit, cfg.cg_tol,
+                       1 if cfg.jacobi else 0, 0, 0)
+        it = api.SeqIter(c.h, self.work.data_ptr(), self.spins.data_ptr(), self.theta.data_ptr(),
+                         self.tanh.data_ptr(), self.lp.data_ptr(), self.R.data_ptr(), self.B,
+                         cfg.sweeps_per_iter, tg, o, ctypes.pointer(self.rng_dev),
+                         self.stats_it.data_ptr())
+        self._keep = getattr(self, "_keep", {})
+        self._keep[kind] = (prev, prev2, tg, o, it)
+        return it
 
     def _target_fixed(self, kind, mean_out=None):
         c, cfg, q = self.ctx, self.cfg, self.cfg.q

@@ -1,7 +1,10 @@
 """Many sequences in one graph: the batched schedule (every sequence's
-iteration in one CUDA graph, each on its own stream) and the one-sequence-
-after-another schedule give the same moments, bit for bit, as each sequence
-run alone, and a vanishing probe (q = 0) is skipped with zero moments."""
+iteration in one CUDA graph through cr_batch_run, each sequence on its own
+stream) and the one-sequence-after-another schedule give the same moments,
+bit for bit, as each sequence run alone (also with tuned fused-CG CTA
+counts), a vanishing probe (q = 0) is skipped with zero moments, and
+cr_batch_run itself reproduces the oracle's sequences on a small float64
+instance."""
 
 import numpy as np
 import pytest
@@ -134,3 +137,79 @@ def test_mixed_contexts_of_different_sizes_coexist():
         ctx.sr_step(p, spins, T, R + 0.1 * T[:, 0], 0.5, 1e-2, cg_maxit=10, cg_tol=1e-4)
         ctx.sync_status()
         assert torch.isfinite(torch.view_as_real(p)).all()
+
+
+def test_batch_run_reproduces_the_oracle_sequences():
+    """Two 12-site chains at different momenta advanced by cr_batch_run
+    (float64, Cholesky): walker trajectories bit-identical to the oracle's
+    shared Philox stream and the moments within 1e-8 mu_0, as each sequence
+    alone in smoke()."""
+    from oracle import chebyshev, exact
+    from paper_2103_08804_gb300 import api, batch, driver, synth
+    L, M, B = 12, 12, 256
+    e0 = np.linalg.eigvalsh(exact.hamiltonian(L, 1, 1.0, exact.sector_basis(L)))[0]
+    specs, refs = [], []
+    for k, q in enumerate(((np.pi, 0.0), (np.pi / 2, 0.0))):
+        kw = dict(Lx=L, Ly=1, M=M, q=q, n_moments=3, n_iter=2, shift=1e-3, dgamma=0.5, E0=e0,
+                  a=5.0, Wp=0.9875, n_therm=2, n_therm_ref=4, seed=10 + 2 * k, seed_ref=11 + 2 * k)
+        psi = synth.rbm_params(20 + k, L, M, 0.05)
+        s_fit, s_ref = synth.sz0_spins(30 + k, B, L), synth.sz0_spins(40 + k, B, L)
+        specs.append(batch.SeqSpec(f"q{k}", driver.SeqConfig(solver=api.SOLVE_CHOLESKY, **kw), psi,
+                                   s_fit, s_ref))
+        refs.append(chebyshev.run_sampled(chebyshev.Config(**kw), psi, s_fit, s_ref))
+    b = batch.Batch(specs, prec=api.FP64, tune=False)
+    b.start()
+    for n in (1, 2):
+        b.fit(n)
+    for ctx in b.ctxs:
+        ctx.sync_status()
+    assert b.graph_launches > 0
+    for seq, ref in zip(b.seqs, refs):
+        assert np.array_equal(host(seq.spins), ref.spins_fit)
+        mu = host(seq.mu)
+        assert np.max(np.abs(mu - np.array(ref.mu))) < 1e-8 * abs(ref.mu[0])
+
+
+def test_tuned_fused_cg_ctas_keep_batched_equal_to_alone():
+    """Mixed contexts (the fused CG) with a smaller CTA count: the batched
+    graph equals each sequence run alone with the same CTA count, bit for
+    bit; a different CTA count changes the sums' grouping only (rounding)."""
+    import torch
+    from gpu_common import dev
+    from paper_2103_08804_gb300 import api, batch, driver, synth
+    specs = _specs()[3:5]
+    b = batch.Batch(specs, prec=api.MIXED, tune=False)
+    b.set_ctas([16] * len(b.ctxs))
+    b.start()
+    for n in range(1, 4):
+        b.fit(n)
+    for ctx in b.ctxs:
+        ctx.sync_status()
+    mom = b.moments()
+    for spec in specs:
+        c = spec.cfg
+        ctx = api.Context(c.Lx, c.Ly, c.M, spec.spins_fit.shape[0], api.MIXED)
+        assert ctx.fused_cg()
+        ctx.set_fcg_ctas(16)
+        seq = driver.Sequence(ctx, c, spec.psi, spec.spins_fit, spec.spins_ref, graphs=True)
+        seq.run()
+        ctx.sync_status()
+        assert np.array_equal(mom[spec.name], host(seq.mu)), spec.name
+    # one product with the default and with 16 CTAs
+    N, M, B = 16, 32, 4096
+    ctx = api.Context(N, 1, M, B, api.MIXED)
+    spins = dev(synth.sz0_spins(4, B, N), torch.int8)
+    p0 = dev(synth.rbm_params(5, N, M, 0.1), ctx.cdtype)
+    theta = torch.empty(B, M, dtype=ctx.cdtype, device="cuda")
+    ctx.rbm_logpsi(p0, spins, theta)
+    T = torch.empty_like(theta)
+    ctx.logderiv(p0, spins, theta, tanh_out=T)
+    v = dev(synth.rbm_params(6, N, M, 1.0), torch.complex128)
+    out = {}
+    for n in (0, 16):
+        ctx.set_fcg_ctas(n)
+        out[n] = host(ctx.sr_sv(spins, T, v, 1e-2))
+    ctx.sync_status()
+    assert np.max(np.abs(out[16] - out[0])) < 1e-6 * np.max(np.abs(out[0]))
+    with pytest.raises(api.CRError):
+        ctx.set_fcg_ctas(100000)
