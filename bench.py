@@ -511,12 +511,13 @@ WL_TEXT = {
 
 def krylov_300(wl):
     """cheb_gram over 300 sampled columns of all the walkers and the float64
-    generalized eigenproblem of Sec. IV (once per sequence)."""
+    generalized eigenproblem of Sec. IV (once per sequence): the mixed
+    context's tensor-core Gram (timed live, with its tensor-pipe figure)
+    beside the float32 context's FFMA Gram."""
     import torch
 
     from paper_2103_08804_gb300 import api
     Nm, Bref = 300, wl.walkers
-    ctx = api.Context(wl.Lx, wl.Ly, wl.M, 64, prec=api.FP32)
     g = torch.Generator(device="cuda")
     g.manual_seed(7)
     Bm = torch.randn(Nm, Bref, dtype=torch.complex64, device="cuda", generator=g)
@@ -526,19 +527,46 @@ def krylov_300(wl):
     mu = torch.zeros(2 * Nm, dtype=torch.complex128, device="cuda")
     poles = torch.zeros(Nm, dtype=torch.float64, device="cuda")
     wts = torch.zeros(Nm, dtype=torch.float64, device="cuda")
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    torch.cuda.synchronize()
-    ev[0].record()
-    ctx.cheb_gram(Bm, HBm, G, H)
-    ev[1].record()
-    ctx.cheb_krylov(G, H, 1e-10, 2 * Nm, mu, poles, wts)
-    ev[2].record()
-    torch.cuda.synchronize()
-    ctx.sync_status()
-    return {"gram_ms": ev[0].elapsed_time(ev[1]), "eigen_ms": ev[1].elapsed_time(ev[2]),
-            "note": "cheb_gram over 300 columns x the walkers, then cheb_krylov (pseudo-inverse, "
-                    "generalized eigenproblem, 600 corrected moments); once per sequence, not in "
-                    "the per-moment steps"}
+    out = {}
+    for name, prec in (("mixed", api.MIXED), ("fp32", api.FP32)):
+        ctx = api.Context(wl.Lx, wl.Ly, wl.M, 64, prec=prec)
+        ctx.cheb_gram(Bm, HBm, G, H)  # sizes the mixed path's scratch
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        reps = 5 if prec == api.MIXED else 1
+        if prec == api.MIXED:
+            ctx.time_kernel("gram", reps)
+        ev[0].record()
+        for _ in range(reps):
+            ctx.cheb_gram(Bm, HBm, G, H)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / reps
+        out[f"gram_ms_{name}"] = ms
+        if prec == api.MIXED:
+            kt = ctx.kernel_times()
+            ctx.time_kernel(None, 0)
+            kms = float(np.mean(kt)) if len(kt) else None
+            flops = 2 * 8.0 * Nm * Nm * Bref
+            out["gram_tc"] = {
+                "kernel": "sgram_tc_kernel (G and H' tiles over K segments)",
+                "kernel_ms": kms, "algorithmic_tflops": flops / (kms * 1e9) if kms else None,
+                "peak_tflops": float(measured_peaks()[0]["bf16_tflops"]),
+                "note": "algorithmic flops 8 Nm^2 B per matrix (G, H'); the three-term splits "
+                        "execute 6x that on the tensor cores; peak: MEASURED_PEAKS.json "
+                        "bf16_tflops (burst)"}
+            ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev2[0].record()
+            ctx.cheb_krylov(G, H, 1e-10, 2 * Nm, mu, poles, wts)
+            ev2[1].record()
+            torch.cuda.synchronize()
+            out["eigen_ms"] = ev2[0].elapsed_time(ev2[1])
+        ctx.sync_status()
+    out["gram_ms"] = out["gram_ms_mixed"]
+    out["note"] = ("cheb_gram over 300 columns x the walkers, then cheb_krylov (pseudo-inverse, "
+                   "generalized eigenproblem, 600 corrected moments); once per sequence, not in "
+                   "the per-moment steps")
+    return out
 
 
 def run_ours(args):

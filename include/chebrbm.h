@@ -26,8 +26,9 @@
  *     unless a comment says "host". The library never frees caller memory.
  *     The context owns only its workspace, allocated once in cr_create, so
  *     the hot calls allocate nothing and can be captured in a CUDA graph.
- *     The one exception is cheb_krylov (called once per sequence), which
- *     sizes its float64 scratch on first use.
+ *     The exceptions are cheb_krylov and, in CR_MIXED contexts, cheb_gram
+ *     (called once per sequence or momentum), which size their scratch on
+ *     first use (and grow it for larger inputs).
  *   Streams. Every call is asynchronous on the context's stream; results
  *     are valid after that stream is synchronised.
  *   Precision. "complex" arrays are interleaved (re, im) in the context's
@@ -217,6 +218,7 @@ cr_status cr_sync_status(cr_ctx* ctx);
 #define CR_KERNEL_CHOL 7    /* blocked Cholesky factor (potrf, trsm, syrk) */
 #define CR_KERNEL_TRSV 8    /* triangular solves of the refinement */
 #define CR_KERNEL_FCG 9     /* fused CG solve (mixed contexts: one launch per solve) */
+#define CR_KERNEL_GRAM 10   /* Krylov Gram G, H on the tensor cores (mixed contexts) */
 long long cr_n_launches(const cr_ctx* ctx);
 cr_status cr_time_kernel(cr_ctx* ctx, int kernel_id, int capacity);
 int cr_kernel_times(cr_ctx* ctx, float* ms_out, int capacity);
@@ -479,7 +481,15 @@ cr_status cheb_moment(cr_ctx* ctx, const cr_state* state, const double* beta, do
 /* Sec. IV estimators: G_nm = <conj(B_n) B_m>, H_nm = <conj(B_n) HB_m>, then
    H <- (H + H^dag)/2. Bmat, HBmat complex [Nm][ld] (row n = column B_n over
    the B samples, leading dimension ld >= B); G_out, H_out complex128
-   [Nm][Nm] (device).  HBmat and H_out may both be NULL (G only). */
+   [Nm][Nm] (device).  HBmat and H_out may both be NULL (G only).
+   CR_FP64 / CR_FP32: products in the storage precision, sums in float64.
+   CR_MIXED: both contractions on the tensor cores (tcgen05) from three-term
+   bf16 splits of the float32 values with float32 accumulation over walker
+   chunks and K segments, float64 across segments (about float32 accuracy);
+   G is Hermitian by construction (upper triangle mirrored, real diagonal).
+   The mixed path sizes its device scratch on first use: bf16 planes of
+   6 * 2 Nm (padded to 256) * B bytes per matrix and the per-segment sums;
+   a failed allocation is CR_ENOMEM. */
 cr_status cheb_gram(cr_ctx* ctx, const void* Bmat, const void* HBmat, int Nm, int B, int ld,
                     double* G_out, double* H_out);
 

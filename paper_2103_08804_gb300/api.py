@@ -34,7 +34,7 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "sym_h_workspace_bytes", "sym_hbtilde", "cheb_init_params", "sr_sv", "cr_fused_cg",
            "cr_set_fcg_ctas", "cr_batch_run")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
-          "chol": 7, "trsv": 8, "fcg": 9}
+          "chol": 7, "trsv": 8, "fcg": 9, "gram": 10}
 
 
 class Lattice(ctypes.Structure):

@@ -194,6 +194,14 @@ struct cr_ctx {
     unsigned char* Xt;       // bf16 hi/lo planes of X^T (mixed explicit S only)
     int2* gtiles;            // lower-triangle blocks of G (mixed explicit S only)
     int n_gtiles;
+    // Krylov Gram on the tensor cores (mixed): sized on first use
+    unsigned char* gram_x;   // bf16 planes of the B and HB columns
+    size_t gram_x_cap;
+    double* gram_part;       // per-segment sums
+    size_t gram_part_cap;
+    int2* gram_tiles;
+    size_t gram_tiles_cap;
+    int gram_key;            // 2 Nm + (H wanted) of the tile list held, 0 if none
     long long n_launches;    // kernels launched so far
     cr_ktimer kt;
     // fused CG solve (cg_fused.cu; mixed contexts with N, M <= 256)
@@ -237,6 +245,8 @@ size_t chol_factor_bytes(const cr_ctx* c);
 size_t chol_cgpart_len();
 cr_status chol_factor(cr_ctx* c);
 cr_status chol_refine_solve(cr_ctx* c, const double* F, int maxit);
+cr_status launch_gram_tc(cr_ctx* c, const void* Bm, const void* HBm, int Nm, int B, int ld,
+                         double* G, double* H);
 cr_status launch_sbuild_tc(cr_ctx* c, const int8_t* spins, const void* T, int B,
                            const double* redO, double shift);
 void launch_smirror(cr_ctx* c);  // S[k][l] = conj(S[l][k]) for k < l

@@ -230,7 +230,8 @@ extern "C" cr_status cr_destroy(cr_ctx* c) {
     void* ptrs[] = {c->d_status, c->d_bonds, c->theta_tmp, c->lp_tmp, c->u_tmp, c->partial,
                     c->red, c->F, c->cg, c->p_lo, c->cgpart, c->scal, c->S, c->O_tmp, c->kry,
                     c->Lf, c->Xt, c->gtiles, c->fcg_a1, c->fcg_b2, c->fcg_v2, c->fcg_vab,
-                    c->fcg_part, c->fcg_psc, c->fcg_bar};
+                    c->fcg_part, c->fcg_psc, c->fcg_bar, c->gram_x, c->gram_part,
+                    c->gram_tiles};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int s = 0; s < 2; ++s) {

@@ -58,6 +58,7 @@ extern "C" cr_status cheb_gram(cr_ctx* ctx, const void* Bmat, const void* HBmat,
     CR_CHECK_ARG(Nm >= 1 && B >= 1 && ld >= B, "cheb_gram: bad sizes");
     CR_CHECK_ARG(Bmat && G_out && ((HBmat && H_out) || (!HBmat && !H_out)),
                  "cheb_gram: null array (HBmat and H_out are both given or both NULL)");
+    if (ctx->prec == CR_MIXED) return launch_gram_tc(ctx, Bmat, HBmat, Nm, B, ld, G_out, H_out);
     dim3 g((Nm + 15) / 16, (Nm + 15) / 16);
     if (ctx->prec == CR_FP64)
         CR_LAUNCH(ctx, CR_K_OTHER, gram_kernel<double><<<g, dim3(16, 16), 0, ctx->stream>>>(

@@ -492,13 +492,39 @@ __global__ void xt_prep_kernel(const int8_t* __restrict__ spins, const cpx<float
     if (NPL == 3) *reinterpret_cast<uint4*>(Xt + 2 * plane_bytes + off) = pack8(t2);
 }
 
+// Arguments of sgram_tc_kernel.  A work item is one tile (rt, ct) of G over
+// one K segment of kseg walker tiles; items run segment-major (item i:
+// segment i / ntiles, tile i % ntiles), so that CTAs running at the same
+// time share operand tiles in L2.  tiles[t] = (rt, ct + 65536 op): op-1
+// tiles take their column operand from xb (the second matrix of X^T Y).
+struct GramArgs {
+    const unsigned char* xa;  // planes of the row operand
+    const unsigned char* xb;  // planes of the column operand of op-1 tiles
+    size_t plane_bytes;
+    int nkc_max;              // walker tiles per row block in the planes
+    int kseg, nseg;           // walker tiles per item, K segments per tile
+    const int2* tiles;
+    int ntiles;
+    // explicit S (part == nullptr): S = G / B - conj(Obar) Obar^T + shift I
+    int P, B;
+    const double* redO;
+    double shift;
+    double* S;
+    // otherwise the raw float32 sums of every item, complex128
+    // part[((op * nseg + seg) * Nm + n) * Nm + m], n, m < Nm
+    double* part;
+    int Nm;
+    int* status;
+};
+
 template <int NPL>
-__global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
-    const unsigned char* __restrict__ Xt, size_t plane_bytes, int nkc_max, int nkc,
-    const int2* __restrict__ tiles, int ntiles, int P, int B, const double* __restrict__ redO_,
-    double shift, double* __restrict__ S_, int* __restrict__ status) {
+__global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(const GramArgs a) {
     using G = SGram<NPL>;
     constexpr int NSTG = G::NSTG, TILE = G::TILE, KPC = G::CH / G::KC;  // tiles per chunk
+    const size_t plane_bytes = a.plane_bytes;
+    const int nkc_max = a.nkc_max, kseg = a.kseg, ntiles = a.ntiles;
+    const int2* __restrict__ tiles = a.tiles;
+    int* __restrict__ status = a.status;
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t* full = (uint64_t*)(sm + NSTG * G::STAGE);
     uint64_t* empty = full + NSTG;      // [NSTG] MMAs reading a stage done
@@ -522,8 +548,9 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = *slot;
-    const int nchunk = (nkc + KPC - 1) / KPC;
-    const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int nchunk = (kseg + KPC - 1) / KPC;
+    const int nitems = ntiles * a.nseg;
+    const int nmine = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     // a bounded wait that also gives up once the other role has aborted
     auto wait = [&](uint64_t* bar, uint32_t par) {
         for (int i = 0; i < 64; ++i) {
@@ -539,7 +566,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
             // One flat sequence of stages over all tiles of this CTA, so the
             // copies run NSTG - 1 stages ahead across tile boundaries too.
             const uint32_t idesc = tc::make_idesc_bf16(128, 256);
-            const int total = nmine * nkc;
+            const int total = nmine * kseg;
             uint32_t pend = 0, pend_par = 0;
             int last_g = -1;  // last stage whose MMAs were committed
             bool ok = true;
@@ -548,27 +575,31 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
             auto load = [&](int g) {
                 const uint32_t b = g % NSTG;
                 if (g >= NSTG && !wait(&empty[b], ((g - NSTG) / NSTG) & 1)) return false;
-                const int tile = blockIdx.x + (g / nkc) * gridDim.x, kc = g % nkc;
-                const int rt = tiles[tile].x, ct = tiles[tile].y;
+                const int item = blockIdx.x + (g / kseg) * gridDim.x;
+                const int2 tl = tiles[item % ntiles];
+                const int kc = (item / ntiles) * kseg + g % kseg;
+                const int rt = tl.x, ct = tl.y & 0xffff;
+                const unsigned char* xb = (tl.y >> 16) ? a.xb : a.xa;
                 pend |= 1u << b;
                 pend_par = (pend_par & ~(1u << b)) | (((uint32_t)(g / NSTG) & 1u) << b);
                 unsigned char* st = sm + (size_t)b * G::STAGE;
                 tc::mbar_expect_tx(&full[b], (uint32_t)G::STAGE);
                 for (int pl = 0; pl < NPL; ++pl) {
-                    const unsigned char* src = Xt + (size_t)pl * plane_bytes;
-                    tc::bulk_g2s(st + pl * TILE, src + ((size_t)rt * nkc_max + kc) * TILE, TILE,
-                                 &full[b]);
+                    tc::bulk_g2s(st + pl * TILE,
+                                 a.xa + (size_t)pl * plane_bytes + ((size_t)rt * nkc_max + kc) * TILE,
+                                 TILE, &full[b]);
                     for (int q = 0; q < 2; ++q)
                         tc::bulk_g2s(st + NPL * TILE + (pl * 2 + q) * TILE,
-                                     src + ((size_t)(2 * ct + q) * nkc_max + kc) * TILE, TILE,
-                                     &full[b]);
+                                     xb + (size_t)pl * plane_bytes +
+                                         ((size_t)(2 * ct + q) * nkc_max + kc) * TILE,
+                                     TILE, &full[b]);
                 }
                 return true;
             };
             for (int g = 0; g < NSTG - 1 && g < total && ok; ++g) ok = load(g);
             for (int g = 0; g < total && ok; ++g) {
-                const int kc = g % nkc, b = g % NSTG;
-                const int gc = (g / nkc) * nchunk + kc / KPC, first = (kc % KPC) == 0;
+                const int kc = g % kseg, b = g % NSTG;
+                const int gc = (g / kseg) * nchunk + kc / KPC, first = (kc % KPC) == 0;
                 const uint32_t h = gc & 1;
                 // the TMEM half of chunk gc was last used by chunk gc - 2
                 if (first && gc >= 2 && !wait(&drained[h], ((gc - 2) >> 1) & 1)) {
@@ -596,7 +627,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
                 }
                 tc::commit(&empty[b]);
                 last_g = g;
-                if ((kc + 1) % KPC == 0 || kc + 1 == nkc) tc::commit(&cdone[h]);
+                if ((kc + 1) % KPC == 0 || kc + 1 == kseg) tc::commit(&cdone[h]);
                 if (g + NSTG - 1 < total && !load(g + NSTG - 1)) ok = false;
             }
             if (!ok) {
@@ -619,13 +650,15 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
         // own error).
         const int lb = warp & 3, c2 = (warp - 1) >> 2, odd = lane & 1;
         const int row = 32 * lb + lane;
-        const cpx<double>* redO = (const cpx<double>*)redO_;
-        cpx<double>* S = (cpx<double>*)S_;
-        const double inv = 1.0 / B;
+        const cpx<double>* redO = (const cpx<double>*)a.redO;
+        cpx<double>* S = (cpx<double>*)a.S;
+        const int P = a.P;
+        const double inv = 1.0 / a.B;
         bool ok = true;
         for (int ti = 0; ti < nmine && ok; ++ti) {
-            const int tile = blockIdx.x + ti * gridDim.x;
-            const int rt = tiles[tile].x, ct = tiles[tile].y;
+            const int item = blockIdx.x + ti * gridDim.x;
+            const int2 tl = tiles[item % ntiles];
+            const int rt = tl.x, ct = tl.y & 0xffff;
             float acc[8][4][2];  // [16-column chunk][entry][Re, Im]
 #pragma unroll
             for (int ch = 0; ch < 8; ++ch)
@@ -664,6 +697,23 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
                              : "memory");
             }
             if (!ok) break;
+            if (a.part) {
+                // raw sums of this item: n = row pair, m = column
+                const int n = 64 * rt + (row >> 1), Nm = a.Nm;
+                cpx<double>* out = (cpx<double>*)a.part +
+                                   (size_t)((tl.y >> 16) * a.nseg + item / ntiles) * Nm * Nm;
+                if (n < Nm) {
+#pragma unroll
+                    for (int ch = 0; ch < 8; ++ch)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int m = 128 * ct + 64 * c2 + 8 * ch + 4 * odd + q;
+                            if (m < Nm)
+                                out[(size_t)n * Nm + m] = {(double)acc[ch][q][0], (double)acc[ch][q][1]};
+                        }
+                }
+                continue;
+            }
             // tile done: S = acc / B - conj(Obar_k) Obar_l (+ shift)
             const int k = 64 * rt + (row >> 1);
             if (k < P) {
@@ -676,7 +726,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(
                         if (l < P) {
                             const cpx<double> g = {(double)acc[ch][q][0], (double)acc[ch][q][1]};
                             cpx<double> val = inv * g - obk * (inv * redO[l]);
-                            if (k == l) val.x += shift;
+                            if (k == l) val.x += a.shift;
                             S[(size_t)k * P + l] = val;
                         }
                     }
@@ -704,6 +754,80 @@ __global__ void smirror_kernel(double* __restrict__ S_, int P) {
     for (int j = ty; j < 32; j += 8) {
         const int r = by * 32 + j, c = bx * 32 + tx;  // destination (row by, col bx)
         if (r < P && c < P && r < c) S[(size_t)r * P + c] = conj(tl[tx][j]);
+    }
+}
+
+// ---------------------------------------------- Krylov Gram (Sec. IV)
+//
+// G = B^dag B / B_s and H = B^dag HB / B_s of cheb_gram on the tensor cores:
+// the complex columns B_n (and HB_n) become rows 2n (real part) and 2n + 1
+// (imaginary part) of a real matrix X (Y), split into three bf16 planes as
+// for the explicit S, and sgram_tc_kernel forms X^T X and X^T Y over K
+// segments of the samples.  gram_reduce_kernel adds the segments in float64
+// in a fixed order, scales by 1/B_s, and writes G (Hermitian by construction:
+// upper triangle mirrored, real diagonal) and (H + H^dag)/2.
+
+// Planes of X from the columns Bm[n * ld + s] (complex64): row 2n + im,
+// walkers s; rows past 2 Nm and walkers past B are zero.
+template <int NPL>
+__global__ void gram_prep_kernel(const cpx<float>* __restrict__ Bm, int Nm, int B, int ld, int nrb,
+                                 int nkc, size_t plane_bytes, unsigned char* __restrict__ X) {
+    using G = SGram<NPL>;
+    constexpr int NG = G::KC / 8;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)nrb * nkc * NG * 128) return;
+    const int r = (int)(idx % 128), grp = (int)((idx / 128) % NG);
+    const size_t rest = idx / (128 * NG);
+    const int kc = (int)(rest % nkc), rb = (int)(rest / nkc);
+    const int row = rb * 128 + r, n = row >> 1, im = row & 1;
+    __nv_bfloat16 t0[8], t1[8], t2[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int s = kc * G::KC + grp * 8 + q;
+        float x = 0.f;
+        if (n < Nm && s < B) {
+            const cpx<float> v = Bm[(size_t)n * ld + s];
+            x = im ? v.y : v.x;
+        }
+        if (NPL == 3) {
+            split3(x, &t0[q], &t1[q], &t2[q]);
+        } else {
+            t0[q] = __float2bfloat16_rn(x);
+            t1[q] = __float2bfloat16_rn(x - __bfloat162float(t0[q]));
+        }
+    }
+    const size_t off = ((size_t)rb * nkc + kc) * G::TILE + tc::kmajor_offset(r, grp * 8, G::KC);
+    *reinterpret_cast<uint4*>(X + off) = pack8(t0);
+    *reinterpret_cast<uint4*>(X + plane_bytes + off) = pack8(t1);
+    if (NPL == 3) *reinterpret_cast<uint4*>(X + 2 * plane_bytes + off) = pack8(t2);
+}
+
+__global__ void gram_reduce_kernel(const double* __restrict__ part_, int nseg, int Nm, int B,
+                                   double* __restrict__ G_, double* __restrict__ H_) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= Nm * Nm) return;
+    const int n = idx / Nm, m = idx % Nm;
+    if (m < n) return;
+    const cpx<double>* part = (const cpx<double>*)part_;
+    const size_t NN = (size_t)Nm * Nm;
+    const double inv = 1.0 / B;
+    cpx<double> g = {0.0, 0.0};
+    for (int sg = 0; sg < nseg; ++sg) g = g + part[sg * NN + (size_t)n * Nm + m];
+    g = inv * g;
+    if (n == m) g.y = 0.0;
+    cpx<double>* Gc = (cpx<double>*)G_;
+    Gc[(size_t)n * Nm + m] = g;
+    Gc[(size_t)m * Nm + n] = conj(g);
+    if (H_) {
+        cpx<double> h1 = {0.0, 0.0}, h2 = {0.0, 0.0};
+        for (int sg = 0; sg < nseg; ++sg) {
+            h1 = h1 + part[(nseg + sg) * NN + (size_t)n * Nm + m];
+            h2 = h2 + part[(nseg + sg) * NN + (size_t)m * Nm + n];
+        }
+        const cpx<double> v = (0.5 * inv) * (h1 + conj(h2));
+        cpx<double>* Hc = (cpx<double>*)H_;
+        Hc[(size_t)n * Nm + m] = v;
+        Hc[(size_t)m * Nm + n] = conj(v);
     }
 }
 
@@ -817,10 +941,22 @@ static cr_status sbuild_tc_t(cr_ctx* c, const int8_t* spins, const void* T, int 
               xt_prep_kernel<NPL><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
                   spins, (const cpx<float>*)T, B, c->N, c->M, c->P, R2, nkc_max, nkc, pb, c->Xt));
     const int grid = c->n_gtiles < c->n_sm ? c->n_gtiles : c->n_sm;
+    GramArgs a{};
+    a.xa = a.xb = c->Xt;
+    a.plane_bytes = pb;
+    a.nkc_max = nkc_max;
+    a.kseg = nkc;
+    a.nseg = 1;
+    a.tiles = c->gtiles;
+    a.ntiles = c->n_gtiles;
+    a.P = c->P;
+    a.B = B;
+    a.redO = redO;
+    a.shift = shift;
+    a.S = c->S;
+    a.status = c->d_status;
     CR_LAUNCH(c, CR_KERNEL_SBUILD,
-              sgram_tc_kernel<NPL><<<grid, GR_THREADS, sgram_smem_t<NPL>(), c->stream>>>(
-                  c->Xt, pb, nkc_max, nkc, c->gtiles, c->n_gtiles, c->P, B, redO, shift, c->S,
-                  c->d_status));
+              sgram_tc_kernel<NPL><<<grid, GR_THREADS, sgram_smem_t<NPL>(), c->stream>>>(a));
     launch_smirror(c);
     return cr_check_launch(c, "explicit S (tensor cores)");
 }
@@ -836,10 +972,110 @@ void launch_smirror(cr_ctx* c) {
     CR_LAUNCH(c, CR_K_OTHER, smirror_kernel<<<dim3(nt, nt), dim3(32, 8), 0, c->stream>>>(c->S, c->P));
 }
 
+// Geometry of the Krylov Gram on the tensor cores (three-plane split): rows
+// of X padded to a multiple of 256, the items' K segments of equal length
+// (walker tiles past B are zero), G tiles on and above the diagonal, all H
+// tiles.
+struct GramGeo {
+    int nrb, nseg, kseg, nkc;
+    size_t plane_bytes, x_bytes, part_bytes;
+    std::vector<int2> tiles;
+};
+
+static GramGeo gram_geometry(const cr_ctx* c, int Nm, int B, bool withH) {
+    using G = SGram<3>;
+    constexpr int KPC = G::CH / G::KC;
+    GramGeo g;
+    const int R2 = ((2 * Nm + 255) / 256) * 256;
+    g.nrb = R2 / 128;
+    const int nrt = (2 * Nm + 127) / 128;
+    for (int op = 0; op < (withH ? 2 : 1); ++op)
+        for (int ct = 0; ct < R2 / 256; ++ct)
+            for (int rt = 0; rt < nrt; ++rt)
+                if (op == 1 || 64 * rt <= 128 * ct + 127) g.tiles.push_back(make_int2(rt, ct + 65536 * op));
+    const int nt = (int)g.tiles.size();
+    const int nch = (B + G::CH - 1) / G::CH;  // 128-walker chunks
+    int nseg = c->n_sm / nt;
+    if (nseg > nch / 4) nseg = nch / 4;      // at least 4 chunks per segment
+    if (nseg < 1) nseg = 1;
+    const int cps = (nch + nseg - 1) / nseg;  // chunks per segment
+    g.nseg = (nch + cps - 1) / cps;
+    g.kseg = cps * KPC;
+    g.nkc = g.nseg * g.kseg;
+    g.plane_bytes = (size_t)g.nrb * g.nkc * G::TILE;
+    g.x_bytes = (withH ? 2 : 1) * 3 * g.plane_bytes;
+    g.part_bytes = (size_t)(withH ? 2 : 1) * g.nseg * Nm * Nm * 16;
+    return g;
+}
+
+static cr_status grow(cr_ctx* c, void** p, size_t* cap, size_t need) {
+    if (*cap >= need) return CR_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, need) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return cr_fail(c, CR_ENOMEM, "cheb_gram: cannot allocate %zu bytes of scratch", need);
+    }
+    *cap = need;
+    return CR_OK;
+}
+
+cr_status launch_gram_tc(cr_ctx* c, const void* Bm, const void* HBm, int Nm, int B, int ld,
+                         double* G, double* H) {
+    GramGeo g = gram_geometry(c, Nm, B, HBm != nullptr);
+    cr_status st = grow(c, (void**)&c->gram_x, &c->gram_x_cap, g.x_bytes);
+    if (st == CR_OK) st = grow(c, (void**)&c->gram_part, &c->gram_part_cap, g.part_bytes);
+    const size_t tcap = c->gram_tiles_cap;
+    if (st == CR_OK) st = grow(c, (void**)&c->gram_tiles, &c->gram_tiles_cap, g.tiles.size() * sizeof(int2));
+    if (c->gram_tiles_cap != tcap) c->gram_key = 0;
+    if (st != CR_OK) return st;
+    const int key = 2 * Nm + (HBm ? 1 : 0);
+    if (c->gram_key != key) {
+        // the tile list changes with Nm only (pageable source: staged before return)
+        if (cudaMemcpyAsync(c->gram_tiles, g.tiles.data(), g.tiles.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            return cr_fail(c, CR_ECUDA, "cheb_gram: tile list copy");
+        c->gram_key = key;
+    }
+    constexpr int NG = SGram<3>::KC / 8;
+    const size_t n = (size_t)g.nrb * g.nkc * NG * 128;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    unsigned char* X = c->gram_x;
+    unsigned char* Y = HBm ? X + 3 * g.plane_bytes : X;
+    CR_LAUNCH(c, CR_K_OTHER, gram_prep_kernel<3><<<nb, 256, 0, c->stream>>>(
+                                 (const cpx<float>*)Bm, Nm, B, ld, g.nrb, g.nkc, g.plane_bytes, X));
+    if (HBm)
+        CR_LAUNCH(c, CR_K_OTHER, gram_prep_kernel<3><<<nb, 256, 0, c->stream>>>(
+                                     (const cpx<float>*)HBm, Nm, B, ld, g.nrb, g.nkc, g.plane_bytes, Y));
+    GramArgs a{};
+    a.xa = X;
+    a.xb = Y;
+    a.plane_bytes = g.plane_bytes;
+    a.nkc_max = g.nkc;
+    a.kseg = g.kseg;
+    a.nseg = g.nseg;
+    a.tiles = c->gram_tiles;
+    a.ntiles = (int)g.tiles.size();
+    a.B = B;
+    a.part = c->gram_part;
+    a.Nm = Nm;
+    a.status = c->d_status;
+    const int items = a.ntiles * a.nseg;
+    const int grid = items < c->n_sm ? items : c->n_sm;
+    CR_LAUNCH(c, CR_KERNEL_GRAM,
+              sgram_tc_kernel<3><<<grid, GR_THREADS, sgram_smem_t<3>(), c->stream>>>(a));
+    CR_LAUNCH(c, CR_K_OTHER, gram_reduce_kernel<<<(Nm * Nm + 255) / 256, 256, 0, c->stream>>>(
+                                 c->gram_part, g.nseg, Nm, B, G, H));
+    return cr_check_launch(c, "cheb_gram (tensor cores)");
+}
+
 // Opt the tensor-core kernels into the shared memory they need; called once
 // per context (not from a hot call, so that hot calls stay capturable).
 cr_status tc_prepare(cr_ctx* c) {
-    if (c->prec == CR_MIXED && (c->flags & CR_CTX_EXPLICIT_S)) {
+    if (c->prec == CR_MIXED) {
+        // explicit S (either split) and the Krylov Gram (three planes)
         cudaError_t e = cudaFuncSetAttribute(sgram_tc_kernel<2>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sgram_smem_t<2>());
