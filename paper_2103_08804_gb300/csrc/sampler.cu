@@ -1,9 +1,10 @@
 // Metropolis sampling of |psi_s|^2 (Sec. III) with S^z-conserving exchange
 // moves on nearest-neighbour bonds.
 //
-// One warp per walker.  Lane l owns the KPL contiguous hidden units
-// [l KPL, (l+1) KPL) of the padded width Mp = 32 KPL and keeps theta and
-// tanh(theta) for them in registers.  The amplitude ratio of a proposal is the
+// One warp per walker.  Lane l owns the KPL hidden units j = 32 k + l
+// (k < KPL) of the padded width Mp = 32 KPL and keeps theta and tanh(theta)
+// for them in registers, so that every table read of a proposal is 32
+// consecutive entries (two 128-byte lines per load instruction).  The amplitude ratio of a proposal is the
 // product over hidden units of (cosh D - s tanh(theta) sinh D) from the bond
 // tables, so the inner loop is complex FMA only; accepted moves update theta
 // and tanh(theta) by the same addition formulas.  Proposals on parallel
@@ -34,7 +35,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(
     cpx<R> th[KPL], T[KPL];
 #pragma unroll
     for (int k = 0; k < KPL; ++k) {
-        int j = lane * KPL + k;
+        int j = 32 * k + lane;
         th[k] = j < M ? theta[(size_t)w * M + j] : cpx<R>{R(0), R(0)};
         T[k] = ctanh_(th[k]);
     }
@@ -54,14 +55,14 @@ __global__ void __launch_bounds__(128) sweep_kernel(
         const int si = sg[bd.x];
         if (si == sg[bd.y]) continue;  // parallel: no-op, counts as rejected
         const R s = R(si);
-        const cpx<R>* chr = Cht + (size_t)b * Mp + lane * KPL;
-        const cpx<R>* shr = Sht + (size_t)b * Mp + lane * KPL;
+        const cpx<R>* chr = Cht + (size_t)b * Mp + lane;
+        const cpx<R>* shr = Sht + (size_t)b * Mp + lane;
         cpx<R> ch[KPL], sh[KPL], f[KPL];
         cpx<R> pl = {R(1), R(0)};
 #pragma unroll
         for (int k = 0; k < KPL; ++k) {
-            ch[k] = ldg(chr + k);
-            sh[k] = ldg(shr + k);
+            ch[k] = ldg(chr + 32 * k);
+            sh[k] = ldg(shr + 32 * k);
             cpx<R> ts = T[k] * sh[k];
             f[k] = {ch[k].x - s * ts.x, ch[k].y - s * ts.y};
             pl = pl * f[k];
@@ -73,10 +74,10 @@ __global__ void __launch_bounds__(128) sweep_kernel(
         const R ratio2 = abs2(e) * abs2(pw);
         const R u = (R(ua >> 9) + R(0.5)) * R(1.1920928955078125e-07);
         if (u < ratio2) {
-            const cpx<R>* dr = Dt + (size_t)b * Mp + lane * KPL;
+            const cpx<R>* dr = Dt + (size_t)b * Mp + lane;
 #pragma unroll
             for (int k = 0; k < KPL; ++k) {
-                cpx<R> d = ldg(dr + k);
+                cpx<R> d = ldg(dr + 32 * k);
                 th[k] = {th[k].x - s * d.x, th[k].y - s * d.y};
                 cpx<R> tc = T[k] * ch[k];
                 T[k] = cdiv(cpx<R>{tc.x - s * sh[k].x, tc.y - s * sh[k].y}, f[k]);
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(
     cpx<R> lp = {R(0), R(0)};
 #pragma unroll
     for (int k = 0; k < KPL; ++k) {
-        int j = lane * KPL + k;
+        int j = 32 * k + lane;
         if (j < M) {
             theta[(size_t)w * M + j] = th[k];
             lp = lp + clncosh2_(th[k]);
