@@ -36,7 +36,9 @@ equations in the paper's order; library primitives (matrix products,
                descent (Sec. I) with the metric S of Sec. III.
   symmetry  -- translation and rotation projection of the local sequence
                onto every momentum of the square lattice (Appendix A).
+  extrapolate -- higher moments from the known ones by linear prediction
+               (Sec. VI; the method of the cited Chebyshev-MPS work).
 """
 
 from . import (lattice, philox, rbm, sampler, target, sr, exact, chebyshev, krylov,  # noqa: F401
-               spectrum, groundstate, symmetry)
+               spectrum, groundstate, symmetry, extrapolate)
