@@ -569,6 +569,39 @@ def krylov_300(wl):
     return out
 
 
+def extrapolation_report(n_seq=36, n_known=300, order=100, n_out=3000):
+    """cheb_extrapolate (linear prediction, Sec. VI) on n_seq synthetic
+    moment sequences whose continuation is known: each the moments of 40
+    Lorentzian-broadened poles, mu_n = sum_k w_k r_k^n cos(n theta_k)."""
+    import torch
+
+    from paper_2103_08804_gb300 import api
+    g = np.random.Generator(np.random.Philox(11))
+    n = np.arange(n_out)
+    mu = np.empty((n_seq, n_out), dtype=np.complex128)
+    for s in range(n_seq):
+        th = g.uniform(0.05, np.pi - 0.05, 40)
+        w = g.exponential(1.0, 40)
+        r = 1.0 - g.uniform(1e-4, 5e-3, 40)
+        mu[s] = ((w[:, None] * r[:, None] ** n) * np.cos(np.outer(th, n))).sum(0) / w.sum()
+    ctx = api.Context(4, 1, 4, 8, prec=api.FP64)
+    x = torch.from_numpy(np.ascontiguousarray(mu[:, :n_known])).cuda()
+    out = ctx.cheb_extrapolate(x, order, n_known // 2, n_out)  # sizes the scratch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = ctx.cheb_extrapolate(x, order, n_known // 2, n_out)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    got = out.cpu().numpy()
+    err = float(np.max(np.abs(got - mu)) / np.max(np.abs(mu[:, 0])))
+    return {"ms": e0.elapsed_time(e1), "sequences": n_seq, "known": n_known, "order": order,
+            "predicted_to": n_out, "max_error_vs_closed_form": err,
+            "note": "one launch, one CTA per sequence, float64: normal equations, Cholesky, "
+                    "Aberth roots, Vandermonde LU, prediction; error relative to mu_0"}
+
+
 def run_ours(args):
     import torch
 
@@ -588,6 +621,7 @@ def run_ours(args):
     if rank == 0 and not args.no_accuracy:
         merr = moment_error(args, wl_name, cyc, 16384 if wl_name == "chain64" else 4096)
     kry = krylov_300(wl) if wl_name == "square16" else None
+    lp = extrapolation_report() if rank == 0 and wl_name == "square16" else None
     cgkeys = ("cg_iters_mean", "cg_iters_max", "cg_rel_residual_median", "cg_rel_residual_max",
               "cg_truncated_fraction", "cg_note")
     out = {
@@ -629,6 +663,8 @@ def run_ours(args):
         out["mixed_over_plain"] = mixed["value"] / plain["value"]
     if kry is not None:
         out["krylov_300"] = kry
+    if lp is not None:
+        out["extrapolation"] = lp
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

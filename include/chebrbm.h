@@ -20,15 +20,16 @@
  *   cheb_moment       beta_n, mu_n and the Krylov columns           (Secs. II, IV)
  *   cheb_gram         sigma_nm = <t_n|t_m>, H_nm = <t_n|H'|t_m>     (Sec. IV)
  *   cheb_krylov       moment correction and projected eigenproblem  (Secs. IV, V)
+ *   cheb_extrapolate  higher moments by linear prediction           (Sec. VI)
  *
  * CONVENTIONS
  *   Memory. Every array argument is a DEVICE pointer owned by the caller,
  *     unless a comment says "host". The library never frees caller memory.
  *     The context owns only its workspace, allocated once in cr_create, so
  *     the hot calls allocate nothing and can be captured in a CUDA graph.
- *     The exceptions are cheb_krylov and, in CR_MIXED contexts, cheb_gram
- *     (called once per sequence or momentum), which size their scratch on
- *     first use (and grow it for larger inputs).
+ *     The exceptions are cheb_krylov, cheb_extrapolate and, in CR_MIXED
+ *     contexts, cheb_gram (called once per sequence or momentum), which
+ *     size their scratch on first use (and grow it for larger inputs).
  *   Streams. Every call is asynchronous on the context's stream; results
  *     are valid after that stream is synchronised.
  *   Precision. "complex" arrays are interleaved (re, im) in the context's
@@ -423,6 +424,31 @@ cr_status cheb_spectrum(cr_ctx* ctx, const double* mu, int Nm, double a, double 
 cr_status cheb_lorentzian(cr_ctx* ctx, const double* poles, const double* weights, int K,
                           double a, double Wp, double eta, const double* omega, int n_omega,
                           double* A_out);
+
+/* Sec. VI (higher moments by extrapolation; the paper cites the method and
+   gives no algorithm): linear prediction of Chebyshev moments (Ganahl et
+   al., Phys. Rev. B 90, 045144 (2014)) with the growing-mode treatment of
+   Barthel, Schollwoeck and White (Phys. Rev. B 79, 245101 (2009)).  For
+   each of n_seq sequences of n_known moments mu_0 .. mu_{N-1}:
+     a = argmin sum_{n=n0}^{N-1} |mu_n + sum_{i=1}^{order} a_i mu_{n-i}|^2
+       (normal equations with a Tikhonov term reg * max_i R_ii, Cholesky);
+     z_k = roots of z^p + a_1 z^{p-1} + ... + a_p (Aberth-Ehrlich);
+     c_k from sum_k c_k z_k^m = mu_{N-p+m}, m < p (LU, partial pivoting);
+     w_k = z_k / |z_k| where |z_k| > 1, else z_k;
+     mu_{N-p+m} = sum_k c_k w_k^m for m >= p.
+   mu: device complex128 [n_seq][n_known]; mu_out: device complex128
+   [n_seq][n_out], the known moments followed by the prediction;
+   roots_out: device complex128 [n_seq][order] (the fitted z_k) or NULL;
+   info_out: device int [n_seq] or NULL: root iterations used, -1 when the
+   root iteration stopped at its limit (500), -2 when a system was
+   singular.  Needs 1 <= order <= 512 and order <= n0 < n_known <= n_out,
+   reg >= 0.  A non-positive Cholesky pivot (reg = 0 on a rank-deficient
+   window) or a singular amplitude system sets CR_ESINGULAR on the device
+   and NaN in that sequence's prediction.  Float64 throughout; sizes its
+   scratch (2 order^2 complex128 per sequence) on first use. */
+cr_status cheb_extrapolate(cr_ctx* ctx, const double* mu, int n_seq, int n_known, int order,
+                           int n0, double reg, int n_out, double* mu_out, double* roots_out,
+                           int* info_out);
 
 /* One sequence's part of a batched run (cr_batch_run): its context and
    device buffers, the target of the projection step being fitted and the

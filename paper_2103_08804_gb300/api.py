@@ -30,7 +30,7 @@ SYMBOLS = ("cr_create", "cr_destroy", "cr_set_stream", "cr_last_error", "cr_sync
            "cheb_local_target", "logderiv", "logpsi_backward", "sr_step", "cheb_moment",
            "cheb_gram", "cheb_krylov", "cr_n_launches", "cr_time_kernel", "cr_kernel_times",
            "logpsi_backward_noalloc", "cr_set_chunks", "cr_max_chunks", "sr_smatrix",
-           "cheb_spectrum", "cheb_lorentzian", "sym_workspace_bytes", "sym_btilde",
+           "cheb_spectrum", "cheb_lorentzian", "cheb_extrapolate", "sym_workspace_bytes", "sym_btilde",
            "sym_h_workspace_bytes", "sym_hbtilde", "cheb_init_params", "sr_sv", "cr_fused_cg",
            "cr_set_fcg_ctas", "cr_batch_run")
 KERNEL = {"sweep": 0, "target": 1, "theta": 2, "ov": 3, "reduce": 4, "cg": 5, "sbuild": 6,
@@ -120,6 +120,7 @@ def load(path=None):
     lib.sym_hbtilde.argtypes = [vp, ctypes.POINTER(State), i, vp, vp, i,
                                 ctypes.POINTER(ctypes.c_double), vp, ctypes.c_size_t, vp, vp]
     lib.cheb_lorentzian.argtypes = [vp, vp, vp, i, d, d, d, vp, i, vp]
+    lib.cheb_extrapolate.argtypes = [vp, vp, i, i, i, i, d, i, vp, vp, vp]
     lib.cr_max_chunks.argtypes = [vp]
     lib.logpsi_backward_noalloc.argtypes = [i, i, i, vp, vp, i, vp, vp, vp, ctypes.c_char_p, i]
     lib.cheb_init_params.argtypes = [vp, i, vp, vp, vp]
@@ -428,6 +429,24 @@ class Context:
                                            1 if jackson else 0, _ptr(omega), omega.numel(),
                                            _ptr(out)), "cheb_spectrum")
         return out
+
+    def cheb_extrapolate(self, mu, order, n0, n_out, reg=1e-12, roots_out=None, info_out=None):
+        """Linear prediction of the moments mu (CUDA complex128 [n_known] or
+        [n_seq, n_known]) to n_out moments; returns complex128 [.., n_out]."""
+        if not (mu.dtype == torch.complex128 and mu.is_cuda and mu.is_contiguous()):
+            raise ValueError("mu: need contiguous CUDA complex128")
+        m2 = mu.reshape(-1, mu.shape[-1])
+        n_seq, n_known = m2.shape
+        out = torch.empty(n_seq, n_out, dtype=torch.complex128, device=mu.device)
+        for t, shape, dt in ((roots_out, (n_seq, order), torch.complex128),
+                             (info_out, (n_seq,), torch.int32)):
+            if t is not None and not (t.dtype == dt and t.is_cuda and t.numel() == shape[0] * (
+                    shape[1] if len(shape) > 1 else 1)):
+                raise ValueError("roots_out / info_out: wrong shape or dtype")
+        self._check(self.lib.cheb_extrapolate(self.h, _ptr(m2), n_seq, n_known, order, n0,
+                                              float(reg), n_out, _ptr(out), _ptr(roots_out),
+                                              _ptr(info_out)), "cheb_extrapolate")
+        return out.reshape(*mu.shape[:-1], n_out)
 
     def cheb_lorentzian(self, poles, weights, a, Wp, eta, omega):
         """The eta-broadened spectral function of the Krylov projection."""

@@ -202,6 +202,8 @@ struct cr_ctx {
     int2* gram_tiles;
     size_t gram_tiles_cap;
     int gram_key;            // 2 Nm + (H wanted) of the tile list held, 0 if none
+    void* lp_work;           // linear-prediction scratch (sized on first use)
+    size_t lp_work_cap;
     long long n_launches;    // kernels launched so far
     cr_ktimer kt;
     // fused CG solve (cg_fused.cu; mixed contexts with N, M <= 256)
@@ -245,6 +247,9 @@ size_t chol_factor_bytes(const cr_ctx* c);
 size_t chol_cgpart_len();
 cr_status chol_factor(cr_ctx* c);
 cr_status chol_refine_solve(cr_ctx* c, const double* F, int maxit);
+// Device scratch that grows on demand (once-per-sequence calls only): frees
+// and reallocates *p when cap < need; CR_ENOMEM with the caller's name.
+cr_status cr_grow(cr_ctx* c, void** p, size_t* cap, size_t need, const char* who);
 cr_status launch_gram_tc(cr_ctx* c, const void* Bm, const void* HBm, int Nm, int B, int ld,
                          double* G, double* H);
 cr_status launch_sbuild_tc(cr_ctx* c, const int8_t* spins, const void* T, int B,

@@ -231,7 +231,7 @@ extern "C" cr_status cr_destroy(cr_ctx* c) {
                     c->red, c->F, c->cg, c->p_lo, c->cgpart, c->scal, c->S, c->O_tmp, c->kry,
                     c->Lf, c->Xt, c->gtiles, c->fcg_a1, c->fcg_b2, c->fcg_v2, c->fcg_vab,
                     c->fcg_part, c->fcg_psc, c->fcg_bar, c->gram_x, c->gram_part,
-                    c->gram_tiles};
+                    c->gram_tiles, c->lp_work};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int s = 0; s < 2; ++s) {
@@ -241,6 +241,20 @@ extern "C" cr_status cr_destroy(cr_ctx* c) {
             if (p) cudaFree(p);
     }
     free(c);
+    return CR_OK;
+}
+
+cr_status cr_grow(cr_ctx* c, void** p, size_t* cap, size_t need, const char* who) {
+    if (*cap >= need) return CR_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, need) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return cr_fail(c, CR_ENOMEM, "%s: cannot allocate %zu bytes of scratch", who, need);
+    }
+    *cap = need;
     return CR_OK;
 }
 

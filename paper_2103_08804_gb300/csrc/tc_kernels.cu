@@ -1008,27 +1008,15 @@ static GramGeo gram_geometry(const cr_ctx* c, int Nm, int B, bool withH) {
     return g;
 }
 
-static cr_status grow(cr_ctx* c, void** p, size_t* cap, size_t need) {
-    if (*cap >= need) return CR_OK;
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-    *cap = 0;
-    if (cudaMalloc(p, need) != cudaSuccess) {
-        (void)cudaGetLastError();
-        *p = nullptr;
-        return cr_fail(c, CR_ENOMEM, "cheb_gram: cannot allocate %zu bytes of scratch", need);
-    }
-    *cap = need;
-    return CR_OK;
-}
-
 cr_status launch_gram_tc(cr_ctx* c, const void* Bm, const void* HBm, int Nm, int B, int ld,
                          double* G, double* H) {
     GramGeo g = gram_geometry(c, Nm, B, HBm != nullptr);
-    cr_status st = grow(c, (void**)&c->gram_x, &c->gram_x_cap, g.x_bytes);
-    if (st == CR_OK) st = grow(c, (void**)&c->gram_part, &c->gram_part_cap, g.part_bytes);
+    cr_status st = cr_grow(c, (void**)&c->gram_x, &c->gram_x_cap, g.x_bytes, "cheb_gram");
+    if (st == CR_OK) st = cr_grow(c, (void**)&c->gram_part, &c->gram_part_cap, g.part_bytes, "cheb_gram");
     const size_t tcap = c->gram_tiles_cap;
-    if (st == CR_OK) st = grow(c, (void**)&c->gram_tiles, &c->gram_tiles_cap, g.tiles.size() * sizeof(int2));
+    if (st == CR_OK)
+        st = cr_grow(c, (void**)&c->gram_tiles, &c->gram_tiles_cap, g.tiles.size() * sizeof(int2),
+                     "cheb_gram");
     if (c->gram_tiles_cap != tcap) c->gram_key = 0;
     if (st != CR_OK) return st;
     const int key = 2 * Nm + (HBm ? 1 : 0);
