@@ -9,6 +9,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+
 #include "chebrbm.h"
 
 #define CR_HD __host__ __device__ __forceinline__
@@ -202,6 +204,11 @@ struct cr_ctx {
     int2* gram_tiles;
     size_t gram_tiles_cap;
     int gram_key;            // 2 Nm + (H wanted) of the tile list held, 0 if none
+    // estimator sums on the tensor cores (mixed contexts; allocated at creation)
+    unsigned char* ored_x;   // bf16 planes of A = [sigma, 1], Y0, Y1
+    double* ored_part;       // per-segment sums
+    int2* ored_tiles;
+    int ored;                // 1 when the path is set up
     void* lp_work;           // linear-prediction scratch (sized on first use)
     size_t lp_work_cap;
     long long n_launches;    // kernels launched so far
@@ -250,6 +257,9 @@ cr_status chol_refine_solve(cr_ctx* c, const double* F, int maxit);
 // Device scratch that grows on demand (once-per-sequence calls only): frees
 // and reallocates *p when cap < need; CR_ENOMEM with the caller's name.
 cr_status cr_grow(cr_ctx* c, void** p, size_t* cap, size_t need, const char* who);
+void ored_sizes(const cr_ctx* c, size_t* x_bytes, size_t* part_bytes, std::vector<int2>* tiles);
+cr_status launch_oreduce_tc(cr_ctx* c, const int8_t* spins, const void* T, const void* g, int B,
+                            double* redR, double* redO);
 cr_status launch_gram_tc(cr_ctx* c, const void* Bm, const void* HBm, int Nm, int B, int ld,
                          double* G, double* H);
 cr_status launch_sbuild_tc(cr_ctx* c, const int8_t* spins, const void* T, int B,

@@ -182,6 +182,14 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
     c->n_sm = 1;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<int2> ot;
+    if (prec == CR_MIXED) {
+        size_t xb, pb;
+        ored_sizes(c, &xb, &pb, &ot);
+        ALLOC(c->ored_x, xb);
+        ALLOC(c->ored_part, pb);
+        ALLOC(c->ored_tiles, ot.size() * sizeof(int2));
+    }
     c->fcg = e == cudaSuccess && fcg_supported(c) ? 1 : 0;
     if (c->fcg) {
         size_t a1, b2, v2p, part;
@@ -211,6 +219,10 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
     e = cudaMemcpy(c->d_bonds, bonds.data(), Nb * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !gt.empty())
         e = cudaMemcpy(c->gtiles, gt.data(), gt.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ot.empty()) {
+        e = cudaMemcpy(c->ored_tiles, ot.data(), ot.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        c->ored = e == cudaSuccess;
+    }
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, 64 * sizeof(double));
     if (e != cudaSuccess || tc_prepare(c) != CR_OK || target_prepare(c) != CR_OK ||
@@ -231,7 +243,7 @@ extern "C" cr_status cr_destroy(cr_ctx* c) {
                     c->red, c->F, c->cg, c->p_lo, c->cgpart, c->scal, c->S, c->O_tmp, c->kry,
                     c->Lf, c->Xt, c->gtiles, c->fcg_a1, c->fcg_b2, c->fcg_v2, c->fcg_vab,
                     c->fcg_part, c->fcg_psc, c->fcg_bar, c->gram_x, c->gram_part,
-                    c->gram_tiles, c->lp_work};
+                    c->gram_tiles, c->lp_work, c->ored_x, c->ored_part, c->ored_tiles};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int s = 0; s < 2; ++s) {

@@ -768,9 +768,14 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
     const int P = c->P;
     double* redR = c->red;
     double* redO = c->red + 2 * (P + 2 + c->M);
-    cr_status s = oreduce(c, true, spins, T, Rv, B, redR, nullptr);
-    if (s != CR_OK) return s;
-    s = oreduce(c, false, spins, T, nullptr, B, redO, nullptr);
+    cr_status s;
+    if (c->ored && !o->cg_precond) {
+        // mixed: both estimator sums in one tensor-core launch
+        s = launch_oreduce_tc(c, spins, T, Rv, B, redR, redO);
+    } else {
+        s = oreduce(c, true, spins, T, Rv, B, redR, nullptr);
+        if (s == CR_OK) s = oreduce(c, false, spins, T, nullptr, B, redO, nullptr);
+    }
     if (s != CR_OK) return s;
     CR_LAUNCH(c, CR_K_OTHER, force_kernel<<<(P + 255) / 256, 256, 0, c->stream>>>(
                                  redR, redO, P, B, o->dgamma, o->mode, c->F, stats, c->d_status));

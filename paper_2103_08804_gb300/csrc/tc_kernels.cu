@@ -495,11 +495,16 @@ __global__ void xt_prep_kernel(const int8_t* __restrict__ spins, const cpx<float
 // Arguments of sgram_tc_kernel.  A work item is one tile (rt, ct) of G over
 // one K segment of kseg walker tiles; items run segment-major (item i:
 // segment i / ntiles, tile i % ntiles), so that CTAs running at the same
-// time share operand tiles in L2.  tiles[t] = (rt, ct + 65536 op): op-1
-// tiles take their column operand from xb (the second matrix of X^T Y).
+// time share operand tiles in L2.  tiles[t] = (rt, ct + 65536 op): the
+// column operand of op-0 tiles is xb0, of op-1 tiles xb1 (two products with
+// one row operand in one launch).  a_exact: the row operand is exact in
+// bf16 (spins, ones) and has one plane, so three products (its plane times
+// each plane of the column operand) replace the split's six.
 struct GramArgs {
-    const unsigned char* xa;  // planes of the row operand
-    const unsigned char* xb;  // planes of the column operand of op-1 tiles
+    const unsigned char* xa;   // planes of the row operand
+    const unsigned char* xb0;  // planes of the column operand of op-0 tiles
+    const unsigned char* xb1;  // planes of the column operand of op-1 tiles
+    int a_exact;
     size_t plane_bytes;
     int nkc_max;              // walker tiles per row block in the planes
     int kseg, nseg;           // walker tiles per item, K segments per tile
@@ -511,9 +516,9 @@ struct GramArgs {
     double shift;
     double* S;
     // otherwise the raw float32 sums of every item, complex128
-    // part[((op * nseg + seg) * Nm + n) * Nm + m], n, m < Nm
+    // part[((op * nseg + seg) * Na + n) * Nb + m], n < Na, m < Nb
     double* part;
-    int Nm;
+    int Na, Nb;
     int* status;
 };
 
@@ -579,15 +584,18 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(const GramArgs 
                 const int2 tl = tiles[item % ntiles];
                 const int kc = (item / ntiles) * kseg + g % kseg;
                 const int rt = tl.x, ct = tl.y & 0xffff;
-                const unsigned char* xb = (tl.y >> 16) ? a.xb : a.xa;
+                const unsigned char* xb = (tl.y >> 16) ? a.xb1 : a.xb0;
                 pend |= 1u << b;
                 pend_par = (pend_par & ~(1u << b)) | (((uint32_t)(g / NSTG) & 1u) << b);
                 unsigned char* st = sm + (size_t)b * G::STAGE;
-                tc::mbar_expect_tx(&full[b], (uint32_t)G::STAGE);
+                const int npa = a.a_exact ? 1 : NPL;  // planes of the row operand
+                tc::mbar_expect_tx(&full[b], (uint32_t)((npa + 2 * NPL) * TILE));
                 for (int pl = 0; pl < NPL; ++pl) {
-                    tc::bulk_g2s(st + pl * TILE,
-                                 a.xa + (size_t)pl * plane_bytes + ((size_t)rt * nkc_max + kc) * TILE,
-                                 TILE, &full[b]);
+                    if (pl < npa)
+                        tc::bulk_g2s(st + pl * TILE,
+                                     a.xa + (size_t)pl * plane_bytes +
+                                         ((size_t)rt * nkc_max + kc) * TILE,
+                                     TILE, &full[b]);
                     for (int q = 0; q < 2; ++q)
                         tc::bulk_g2s(st + NPL * TILE + (pl * 2 + q) * TILE,
                                      xb + (size_t)pl * plane_bytes +
@@ -614,15 +622,29 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(const GramArgs 
                 tc::fence_after_sync();
                 const unsigned char* st = sm + (size_t)b * G::STAGE;
                 const uint32_t a0 = tc::smem_u32(st), b0 = tc::smem_u32(st + NPL * TILE);
+                if (a.a_exact) {
 #pragma unroll
-                for (int ks = 0; ks < G::KC / 16; ++ks) {
+                    for (int ks = 0; ks < G::KC / 16; ++ks) {
+                        const uint64_t ad = tc::make_desc(a0 + ks * 256, 128, 16 * G::KC);
 #pragma unroll
-                    for (int pr = 0; pr < G::NPROD; ++pr) {
-                        const uint64_t ad =
-                            tc::make_desc(a0 + G::pa(pr) * TILE + ks * 256, 128, 16 * G::KC);
-                        const uint64_t bd =
-                            tc::make_desc(b0 + G::pb(pr) * 2 * TILE + ks * 256, 128, 16 * G::KC);
-                        tc::mma_bf16(taddr + h * 256, ad, bd, idesc, !(first && ks == 0 && pr == 0));
+                        for (int pl = 0; pl < NPL; ++pl) {
+                            const uint64_t bd =
+                                tc::make_desc(b0 + pl * 2 * TILE + ks * 256, 128, 16 * G::KC);
+                            tc::mma_bf16(taddr + h * 256, ad, bd, idesc, !(first && ks == 0 && pl == 0));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int ks = 0; ks < G::KC / 16; ++ks) {
+#pragma unroll
+                        for (int pr = 0; pr < G::NPROD; ++pr) {
+                            const uint64_t ad =
+                                tc::make_desc(a0 + G::pa(pr) * TILE + ks * 256, 128, 16 * G::KC);
+                            const uint64_t bd =
+                                tc::make_desc(b0 + G::pb(pr) * 2 * TILE + ks * 256, 128, 16 * G::KC);
+                            tc::mma_bf16(taddr + h * 256, ad, bd, idesc,
+                                         !(first && ks == 0 && pr == 0));
+                        }
                     }
                 }
                 tc::commit(&empty[b]);
@@ -699,17 +721,17 @@ __global__ void __launch_bounds__(GR_THREADS, 1) sgram_tc_kernel(const GramArgs 
             if (!ok) break;
             if (a.part) {
                 // raw sums of this item: n = row pair, m = column
-                const int n = 64 * rt + (row >> 1), Nm = a.Nm;
+                const int n = 64 * rt + (row >> 1), Na = a.Na, Nb = a.Nb;
                 cpx<double>* out = (cpx<double>*)a.part +
-                                   (size_t)((tl.y >> 16) * a.nseg + item / ntiles) * Nm * Nm;
-                if (n < Nm) {
+                                   (size_t)((tl.y >> 16) * a.nseg + item / ntiles) * Na * Nb;
+                if (n < Na) {
 #pragma unroll
                     for (int ch = 0; ch < 8; ++ch)
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const int m = 128 * ct + 64 * c2 + 8 * ch + 4 * odd + q;
-                            if (m < Nm)
-                                out[(size_t)n * Nm + m] = {(double)acc[ch][q][0], (double)acc[ch][q][1]};
+                            if (m < Nb)
+                                out[(size_t)n * Nb + m] = {(double)acc[ch][q][0], (double)acc[ch][q][1]};
                         }
                 }
                 continue;
@@ -942,7 +964,7 @@ static cr_status sbuild_tc_t(cr_ctx* c, const int8_t* spins, const void* T, int 
                   spins, (const cpx<float>*)T, B, c->N, c->M, c->P, R2, nkc_max, nkc, pb, c->Xt));
     const int grid = c->n_gtiles < c->n_sm ? c->n_gtiles : c->n_sm;
     GramArgs a{};
-    a.xa = a.xb = c->Xt;
+    a.xa = a.xb0 = a.xb1 = c->Xt;
     a.plane_bytes = pb;
     a.nkc_max = nkc_max;
     a.kseg = nkc;
@@ -1038,8 +1060,8 @@ cr_status launch_gram_tc(cr_ctx* c, const void* Bm, const void* HBm, int Nm, int
         CR_LAUNCH(c, CR_K_OTHER, gram_prep_kernel<3><<<nb, 256, 0, c->stream>>>(
                                      (const cpx<float>*)HBm, Nm, B, ld, g.nrb, g.nkc, g.plane_bytes, Y));
     GramArgs a{};
-    a.xa = X;
-    a.xb = Y;
+    a.xa = a.xb0 = X;
+    a.xb1 = Y;
     a.plane_bytes = g.plane_bytes;
     a.nkc_max = g.nkc;
     a.kseg = g.kseg;
@@ -1048,7 +1070,7 @@ cr_status launch_gram_tc(cr_ctx* c, const void* Bm, const void* HBm, int Nm, int
     a.ntiles = (int)g.tiles.size();
     a.B = B;
     a.part = c->gram_part;
-    a.Nm = Nm;
+    a.Na = a.Nb = Nm;
     a.status = c->d_status;
     const int items = a.ntiles * a.nseg;
     const int grid = items < c->n_sm ? items : c->n_sm;
@@ -1057,6 +1079,175 @@ cr_status launch_gram_tc(cr_ctx* c, const void* Bm, const void* HBm, int Nm, int
     CR_LAUNCH(c, CR_K_OTHER, gram_reduce_kernel<<<(Nm * Nm + 255) / 256, 256, 0, c->stream>>>(
                                  c->gram_part, g.nseg, Nm, B, G, H));
     return cr_check_launch(c, "cheb_gram (tensor cores)");
+}
+
+// ------------------------------------ estimator sums on the tensor cores
+//
+// The two walker sums of a natural-gradient step (Sec. III),
+//   redR = [sum sigma_i g | sum conj(T_j) g | sum sigma_i conj(T_j) g | sum g | sum |g|^2]
+//   redO = [sum sigma_i   | sum T_j         | sum sigma_i T_j         | B     | B      ]
+// (g = R; the layout of oreduce's rows), as one launch of sgram_tc_kernel:
+// row operand A = [sigma_0 .. sigma_{N-1}, 1] (exact in bf16: one plane),
+// column operands Y0 = [conj(T_j) g, g, |g|^2] (op 0) and Y1 = [T_j, 1]
+// (op 1), split into three bf16 planes; out = sum_s A_k(s) Y_l(s) over K
+// segments, added in float64 by ored_reduce_kernel.  The sums of |T_j|^2
+// (the Jacobi diagonal) are not formed here.
+struct OredGeo {
+    int R2, nrb, nseg, nkc_cap, Na, Nb;
+    size_t plane_bytes, x_bytes, part_bytes;
+    std::vector<int2> tiles;
+};
+
+static OredGeo ored_geometry(const cr_ctx* c) {
+    using G = SGram<3>;
+    constexpr int KPC = G::CH / G::KC;
+    OredGeo g;
+    g.Na = c->N + 1;
+    g.Nb = c->M + 2;
+    const int ra = 2 * g.Na, rb0 = 2 * (c->M + 2), rb1 = 2 * (c->M + 1);
+    const int rmax = ra > rb0 ? ra : rb0;
+    g.R2 = ((rmax + 255) / 256) * 256;
+    g.nrb = g.R2 / 128;
+    const int nrt = (ra + 127) / 128;
+    for (int op = 0; op < 2; ++op) {
+        const int nct = ((op ? rb1 : rb0) + 255) / 256;
+        for (int ct = 0; ct < nct; ++ct)
+            for (int rt = 0; rt < nrt; ++rt) g.tiles.push_back(make_int2(rt, ct + 65536 * op));
+    }
+    const int nt = (int)g.tiles.size();
+    g.nseg = c->n_sm / nt > 1 ? c->n_sm / nt : 1;
+    const int nch = (c->max_walkers + G::CH - 1) / G::CH;
+    g.nkc_cap = g.nseg * ((nch + g.nseg - 1) / g.nseg) * KPC;
+    g.plane_bytes = (size_t)g.nrb * g.nkc_cap * G::TILE;
+    g.x_bytes = 7 * g.plane_bytes;  // A: one plane; Y0, Y1: three each
+    g.part_bytes = (size_t)2 * g.nseg * g.Na * g.Nb * 16;
+    return g;
+}
+
+void ored_sizes(const cr_ctx* c, size_t* x_bytes, size_t* part_bytes, std::vector<int2>* tiles) {
+    OredGeo g = ored_geometry(c);
+    *x_bytes = g.x_bytes;
+    *part_bytes = g.part_bytes;
+    *tiles = g.tiles;
+}
+
+// Planes of A (plane 0 only) and of Y0, Y1 for walker tiles kc < nkc (zero
+// past B): one thread per (row, 8 walkers); T is read once for both Y.
+__global__ void ored_prep_kernel(const int8_t* __restrict__ spins, const cpx<float>* __restrict__ T,
+                                 const cpx<float>* __restrict__ g, int B, int N, int M, int nrb,
+                                 int nkc, int nkc_cap, size_t plane_bytes,
+                                 unsigned char* __restrict__ X) {
+    using G = SGram<3>;
+    constexpr int NG = G::KC / 8;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)nrb * nkc * NG * 128) return;
+    const int r = (int)(idx % 128), grp = (int)((idx / 128) % NG);
+    const size_t rest = idx / (128 * NG);
+    const int kc = (int)(rest % nkc), rb = (int)(rest / nkc);
+    const int row = rb * 128 + r, k = row >> 1, im = row & 1;
+    __nv_bfloat16 a[8], y0[3][8], y1[3][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int s = kc * G::KC + grp * 8 + q;
+        float xa = 0.f, x0 = 0.f, x1 = 0.f;
+        if (s < B) {
+            if (!im) xa = k < N ? (float)spins[(size_t)s * N + k] : (k == N ? 1.f : 0.f);
+            const cpx<float> gs = g[s];
+            cpx<float> v0 = {0.f, 0.f}, v1 = {0.f, 0.f};
+            if (k < M) {
+                const cpx<float> t = T[(size_t)s * M + k];
+                v0 = conj(t) * gs;
+                v1 = t;
+            } else if (k == M) {
+                v0 = gs;
+                v1 = {1.f, 0.f};
+            } else if (k == M + 1) {
+                v0 = {abs2(gs), 0.f};
+            }
+            x0 = im ? v0.y : v0.x;
+            x1 = im ? v1.y : v1.x;
+        }
+        a[q] = __float2bfloat16_rn(xa);  // exact: +-1, 1 or 0
+        split3(x0, &y0[0][q], &y0[1][q], &y0[2][q]);
+        split3(x1, &y1[0][q], &y1[1][q], &y1[2][q]);
+    }
+    const size_t off = ((size_t)rb * nkc_cap + kc) * G::TILE + tc::kmajor_offset(r, grp * 8, G::KC);
+    *reinterpret_cast<uint4*>(X + off) = pack8(a);
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) {
+        *reinterpret_cast<uint4*>(X + (1 + pl) * plane_bytes + off) = pack8(y0[pl]);
+        *reinterpret_cast<uint4*>(X + (4 + pl) * plane_bytes + off) = pack8(y1[pl]);
+    }
+}
+
+__global__ void ored_reduce_kernel(const double* __restrict__ part_, int nseg, int N, int M, int P,
+                                   int Na, int Nb, double* __restrict__ redR_,
+                                   double* __restrict__ redO_) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P + 2 + M) return;
+    cpx<double>* redR = (cpx<double>*)redR_;
+    cpx<double>* redO = (cpx<double>*)redO_;
+    if (k >= P + 2) {
+        redO[k] = {0.0, 0.0};  // sums of |T_j|^2: not formed on this path
+        return;
+    }
+    int n, m;  // (row of A, column of Y)
+    if (k < N) { n = k; m = M; }
+    else if (k < N + M) { n = N; m = k - N; }
+    else if (k < P) { n = (k - N - M) / M; m = (k - N - M) % M; }
+    else { n = N; m = M + (k - P); }
+    const cpx<double>* part = (const cpx<double>*)part_;
+    const size_t NN = (size_t)Na * Nb, e = (size_t)n * Nb + m;
+    cpx<double> r = {0.0, 0.0}, o = {0.0, 0.0};
+    for (int sg = 0; sg < nseg; ++sg) {
+        r = r + part[sg * NN + e];
+        if (k <= P) o = o + part[(nseg + sg) * NN + e];
+    }
+    if (k == P + 1) {
+        // sum |1|^2 = sum 1, the B of entry P
+        for (int sg = 0; sg < nseg; ++sg) o = o + part[(nseg + sg) * NN + (size_t)N * Nb + M];
+        r.y = 0.0;
+    }
+    redR[k] = r;
+    redO[k] = o;
+}
+
+cr_status launch_oreduce_tc(cr_ctx* c, const int8_t* spins, const void* T, const void* g, int B,
+                            double* redR, double* redO) {
+    using G = SGram<3>;
+    constexpr int KPC = G::CH / G::KC, NG = G::KC / 8;
+    OredGeo geo = ored_geometry(c);
+    const int nch = (B + G::CH - 1) / G::CH;
+    const int cps = (nch + geo.nseg - 1) / geo.nseg;
+    const int nseg = (nch + cps - 1) / cps, kseg = cps * KPC, nkc = nseg * kseg;
+    const size_t n = (size_t)geo.nrb * nkc * NG * 128;
+    CR_LAUNCH(c, CR_K_OTHER, ored_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+                                 spins, (const cpx<float>*)T, (const cpx<float>*)g, B, c->N, c->M,
+                                 geo.nrb, nkc, geo.nkc_cap, geo.plane_bytes, c->ored_x));
+    GramArgs a{};
+    a.xa = c->ored_x;
+    a.xb0 = c->ored_x + geo.plane_bytes;
+    a.xb1 = c->ored_x + 4 * geo.plane_bytes;
+    a.a_exact = 1;
+    a.plane_bytes = geo.plane_bytes;
+    a.nkc_max = geo.nkc_cap;
+    a.kseg = kseg;
+    a.nseg = nseg;
+    a.tiles = c->ored_tiles;
+    a.ntiles = (int)geo.tiles.size();
+    a.B = B;
+    a.part = c->ored_part;
+    a.Na = geo.Na;
+    a.Nb = geo.Nb;
+    a.status = c->d_status;
+    const int items = a.ntiles * nseg;
+    const int grid = items < c->n_sm ? items : c->n_sm;
+    CR_LAUNCH(c, CR_KERNEL_REDUCE,
+              sgram_tc_kernel<3><<<grid, GR_THREADS, sgram_smem_t<3>(), c->stream>>>(a));
+    const int len = c->P + 2 + c->M;
+    CR_LAUNCH(c, CR_K_OTHER, ored_reduce_kernel<<<(len + 255) / 256, 256, 0, c->stream>>>(
+                                 c->ored_part, nseg, c->N, c->M, c->P, geo.Na, geo.Nb, redR, redO));
+    return cr_check_launch(c, "estimator sums (tensor cores)");
 }
 
 // Opt the tensor-core kernels into the shared memory they need; called once

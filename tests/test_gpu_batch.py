@@ -84,9 +84,11 @@ def test_per_q_schedule_equals_batched_and_autotune():
 @pytest.mark.parametrize("prec", [1, 2])
 def test_chunk_count_changes_only_the_summation_order(prec):
     # one natural-gradient update on identical inputs with the largest and a
-    # small chunk count: the float64 combination of float32 partial sums in a
-    # different grouping, so the updates agree to float32 rounding (a strong
-    # shift keeps the solve well conditioned)
+    # small chunk count.  float32: the float64 combination of float32 partial
+    # sums in a different grouping, so the updates agree to float32 rounding
+    # (a strong shift keeps the solve well conditioned).  mixed: the estimator
+    # sums run on the tensor cores over K segments and the CG is fused, so
+    # the chunk count does not enter the step at all.
     import torch
     from gpu_common import dev
     from paper_2103_08804_gb300 import api, synth
@@ -109,8 +111,11 @@ def test_chunk_count_changes_only_the_summation_order(prec):
         ctx.sync_status()
         out[n] = host(p - p0)
     d = out[32]
-    assert np.linalg.norm(out[3] - d) < 1e-4 * np.linalg.norm(d)
-    assert not np.array_equal(out[3], d)
+    if prec == 2:
+        assert np.array_equal(out[3], d)
+    else:
+        assert np.linalg.norm(out[3] - d) < 1e-4 * np.linalg.norm(d)
+        assert not np.array_equal(out[3], d)
     with pytest.raises(api.CRError):
         ctx.set_chunks(33)
     with pytest.raises(api.CRError):

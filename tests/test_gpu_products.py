@@ -84,6 +84,64 @@ def test_sv_products_against_explicit_O(prec, shape):
     assert eu < TOL[prec] and es < TOL[prec]
 
 
+def _oracle_estimators(spins, T, R, block=256):
+    """<R>, <|R|^2>, <O> and <O* R> from the explicit O, walker block by block."""
+    B = spins.shape[0]
+    Obar = OR = 0.0
+    for s0 in range(0, B, block):
+        O = rbm.logderiv_from_tanh(spins[s0:s0 + block], T[s0:s0 + block])
+        Obar = Obar + O.sum(axis=0)
+        OR = OR + (np.conj(O) * R[s0:s0 + block, None]).sum(axis=0)
+    return {"mR": R.mean(), "mRR": float(np.mean(np.abs(R) ** 2)), "Obar": Obar / B, "OR": OR / B}
+
+
+# the estimator sums (F, <O>, <R>, <|R|^2>) of one natural-gradient step:
+# float32 path compensated float32 sums, mixed path tensor cores (bf16 splits,
+# float32 accumulation over 128-walker chunks and K segments, float64 across):
+# about 1e-7 of the summed terms; gate 1e-6
+EST_TOL = {"fp32": 1e-6, "mixed": 1e-6}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("shape", [(12, 1, 12, 1000), (8, 8, 128, 4099), (16, 16, 256, 4099)])
+def test_estimators_and_force_against_oracle(prec, shape):
+    """F through the update of a step on a zero RBM: one CG iteration on
+    (S + lambda I) x = F gives x = F |F|^2 / F^dag (S + lambda I) F (the
+    oracle forms F^dag S F matrix-free), and the update writes x into the zero
+    parameters (float32 rounding only); lambda = 1e9 keeps x a scaled F."""
+    from oracle import sr
+    from paper_2103_08804_gb300 import api
+    Lx, Ly, M, B = shape
+    N = Lx * Ly
+    p, cd, npdt = PRECS[prec]
+    spins, T, _ = _inputs(Lx, Ly, M, B, 0.05, 90, npdt)
+    g = np.random.Generator(np.random.Philox(91))
+    R = (1.0 + 0.3 * (g.standard_normal(B) + 1j * g.standard_normal(B))).astype(npdt)
+    est = _oracle_estimators(spins, T, R.astype(np.complex128))
+    F_ref, gamma = sr.force(est, 0.5)
+    ctx = api.Context(Lx, Ly, M, B, prec=p)
+    pr = torch.zeros(ctx.P, dtype=cd, device="cuda")
+    stats = torch.zeros(api.STATS_LEN, dtype=torch.float64, device="cuda")
+    ctx.sr_step(pr, dev(spins, torch.int8), dev(T, cd), dev(R, cd), 0.5, 1e9,
+                solver=api.SOLVE_CG, cg_maxit=1, cg_tol=1e-12, stats_out=stats)
+    ctx.sync_status()
+    st = host(stats)
+    assert st[0] == pytest.approx(gamma, rel=1e-6)
+    assert complex(st[1], st[2]) == pytest.approx(est["mR"], rel=1e-6)
+    assert st[3] == pytest.approx(est["mRR"], rel=1e-6)
+    # F = c (<O* R>/<R> - <O>*) cancels (here R is independent of O): the
+    # error of the two float32-accumulated sums is measured against the size
+    # of the terms that are subtracted
+    c = 0.5 * sr.gamma_cot_gamma(gamma)
+    scale = c * np.max(np.abs(est["OR"] / est["mR"]))
+    blocks = (rbm.logderiv_from_tanh(spins[s0:s0 + 256], T[s0:s0 + 256]) for s0 in range(0, B, 256))
+    fsf = np.vdot(F_ref, sr.sv_matrix_free(blocks, F_ref, 1e9)).real
+    x_ref = F_ref * (np.vdot(F_ref, F_ref).real / fsf)
+    dF = 1e9 * np.max(np.abs(host(pr).astype(np.complex128) - x_ref))
+    print(f"{prec} {shape}: F {dF / scale:.2e} of the terms, {dF / np.max(np.abs(F_ref)):.2e} of F")
+    assert dF / scale < EST_TOL[prec]
+
+
 def test_init_params_match_the_oracle():
     from paper_2103_08804_gb300 import api
     N, M = 12, 12
