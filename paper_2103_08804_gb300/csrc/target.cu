@@ -139,34 +139,58 @@ __global__ void __launch_bounds__(128) hprime_kernel(hp_args<R> A) {
         const R inv_sqrt_n = m_rsqrt(R(A.N));
         xsum = warp_sum(xsum);
         asg = warp_sum(asg);
-        for (int k = lane; k < n_anti; k += 32) {
-            const int b = lst[k];
-            const int2 bd = bonds[b];
-            const int si = sg[bd.x];
-            const R s = R(si);
-            cpx<R> pr = A.ea[2 * b + (si > 0 ? 0 : 1)];
-            const cpx<R>* chc = A.ChT + b;
-            const cpx<R>* shc = A.ShT + b;
-            // the product of M factors is kept as pr * 2^ex, renormalised every
-            // 16 factors, so it cannot overflow or underflow float32
-            int ex = 0;
+        // two bonds per lane at a time (k and k + 32 of the list): two
+        // independent product chains share the C_m, S_m reads and keep twice
+        // the table loads in flight; the sum runs in the list's order
+        for (int k0 = 0; k0 < n_anti; k0 += 64) {
+            int kk[2], bb[2], ex[2] = {0, 0};
+            R sv[2];
+            cpx<R> pr[2];
+            const cpx<R>* chc[2];
+            const cpx<R>* shc[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                kk[u] = k0 + 32 * u + lane;
+                bb[u] = kk[u] < n_anti ? lst[kk[u]] : 0;  // bond 0 as a placeholder
+                const int si = sg[bonds[bb[u]].x];
+                sv[u] = R(si);
+                pr[u] = A.ea[2 * bb[u] + (si > 0 ? 0 : 1)];
+                chc[u] = A.ChT + bb[u];
+                shc[u] = A.ShT + bb[u];
+            }
+            // the products of M factors are kept as pr * 2^ex, renormalised
+            // every 16 factors, so they cannot overflow or underflow float32
             for (int m = 0; m < A.M; ++m) {
-                const cpx<R> ch = ldg(chc + (size_t)m * A.Nb), sh = ldg(shc + (size_t)m * A.Nb);
-                const cpx<R> c1 = Cm[m] * ch, s1 = Sm[m] * sh;
-                pr = pr * cpx<R>{c1.x - s * s1.x, c1.y - s * s1.y};  // cosh(theta - s D) e^{-|Re theta|}
+                const cpx<R> cm = Cm[m], sm = Sm[m];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const cpx<R> ch = ldg(chc[u] + (size_t)m * A.Nb), sh = ldg(shc[u] + (size_t)m * A.Nb);
+                    const cpx<R> c1 = cm * ch, s1 = sm * sh;
+                    // cosh(theta - s D) e^{-|Re theta|}
+                    pr[u] = pr[u] * cpx<R>{c1.x - sv[u] * s1.x, c1.y - sv[u] * s1.y};
+                }
                 if ((m & 15) == 15) {
-                    int e;
-                    frexp(fmax(fabs(pr.x), fabs(pr.y)), &e);
-                    pr = {ldexp(pr.x, -e), ldexp(pr.y, -e)};
-                    ex += e;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        int e;
+                        frexp(fmax(fabs(pr[u].x), fabs(pr[u].y)), &e);
+                        pr[u] = {ldexp(pr[u].x, -e), ldexp(pr[u].y, -e)};
+                        ex[u] += e;
+                    }
                 }
             }
-            if (A.pr.on) {
-                // f(s^{ij}) = f(s) + s (e^{-iq.r_i'} - e^{-iq.r_i}) / sqrt(N)
-                cpx<R> d = phase<R>(bd.y, A.Lx, A.pr.qx, A.pr.qy) - phase<R>(bd.x, A.Lx, A.pr.qx, A.pr.qy);
-                pr = (fs + (s * inv_sqrt_n) * d) * pr;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (kk[u] >= n_anti) continue;
+                if (A.pr.on) {
+                    // f(s^{ij}) = f(s) + s (e^{-iq.r_i'} - e^{-iq.r_i}) / sqrt(N)
+                    const int2 bd = bonds[bb[u]];
+                    cpx<R> d = phase<R>(bd.y, A.Lx, A.pr.qx, A.pr.qy) -
+                               phase<R>(bd.x, A.Lx, A.pr.qx, A.pr.qy);
+                    pr[u] = (fs + (sv[u] * inv_sqrt_n) * d) * pr[u];
+                }
+                off = off + cpx<double>{ldexp((double)pr[u].x, ex[u]), ldexp((double)pr[u].y, ex[u])};
             }
-            off = off + cpx<double>{ldexp((double)pr.x, ex), ldexp((double)pr.y, ex)};
         }
         off = warp_sum(off);
         const double ia = 1.0 / A.a;
