@@ -8,6 +8,7 @@
 
 cr_status tc_prepare(cr_ctx* c);
 cr_status target_prepare(cr_ctx* c);
+cr_status sym_prepare(cr_ctx* c);
 void sgram_geometry(const cr_ctx* c, int* R2, int* nkc_max, size_t* plane_bytes, int* npl);
 std::vector<int2> sgram_tiles(int P);
 
@@ -225,7 +226,7 @@ extern "C" cr_status cr_create(cr_ctx** out, const cr_lattice* lat, int M, int m
     }
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->scal, 0, 64 * sizeof(double));
-    if (e != cudaSuccess || tc_prepare(c) != CR_OK || target_prepare(c) != CR_OK ||
+    if (e != cudaSuccess || tc_prepare(c) != CR_OK || target_prepare(c) != CR_OK || sym_prepare(c) != CR_OK ||
         (c->fcg && fcg_prepare(c) != CR_OK)) {
         cr_destroy(c);
         return CR_ECUDA;

@@ -76,14 +76,29 @@ __global__ void sym_rot_kernel(const cpx<R>* __restrict__ lp, const cpx<R>* __re
 }
 
 // hb[w] = (H' t_n)(s'_w) / psi(s), w = g B + s over the nc transformed
-// configurations, one warp each (Sec. V bonds).  With x_m = Re theta_m(s'),
+// configurations (Sec. V bonds).  With x_m = Re theta_m(s'),
 // C_m = cosh(theta_m) e^{-|x_m|} and S_m = sinh(theta_m) e^{-|x_m|} (both of
 // modulus <= 1),
 //   t_n(s'^{ij}) / psi(s) = e^{Lam} ea_b prod_m (C_m cosh D_bm - s_i S_m sinh D_bm),
 //   Lam = a.s' + M log 2 + sum_m |x_m| - log psi(s),
 // from cosh(theta - s D) = cosh theta cosh D - s sinh theta sinh D and the
-// bond tables D_bm, ea_b of t_n; the product is renormalised every 16 factors
-// and Lam, the diagonal part and the sums are formed in float64.
+// bond tables D_bm, ea_b of t_n; the products are rescaled by a power of
+// two every 16 factors and Lam, the diagonal part and the sums are formed in
+// float64.
+//
+// One lane per configuration: the 32 lanes of a warp walk the same bonds
+// and hidden units in step, so every table read is one broadcast for the
+// whole warp, and a lane keeps GB independent bond products in registers
+// (GB bonds per pass over the hidden units).  Every bond is evaluated and the
+// parallel ones are dropped from the sum, which costs twice the arithmetic
+// of the antiparallel bonds alone but no divergence.  theta of the warp's 32
+// configurations is staged through shared memory MC hidden units at a time
+// (coalesced reads), and C_m, S_m are formed again on every pass.
+constexpr int SYM_MC = 8;
+
+template <typename R>
+CR_HD constexpr int sym_gb() { return sizeof(R) == 4 ? 16 : 8; }
+
 template <typename R>
 __global__ void __launch_bounds__(128) sym_hprime_kernel(
     const int8_t* __restrict__ sp, const cpx<R>* __restrict__ theta, const cpx<R>* __restrict__ lp,
@@ -91,82 +106,107 @@ __global__ void __launch_bounds__(128) sym_hprime_kernel(
     const cpx<R>* __restrict__ ChT, const cpx<R>* __restrict__ ShT, const cpx<R>* __restrict__ ea,
     const int2* __restrict__ bonds_g, int nc, int B, int N, int M, int Mp, int Nb, double J,
     double E0, double a, double Wp, cpx<R>* __restrict__ hb) {
+    constexpr int GB = sym_gb<R>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Nq = (N + 3) & ~3;
     int2* bonds = (int2*)smem_raw;                                   // [Nb]
-    cpx<R>* CSall = (cpx<R>*)(bonds + Nb + (Nb & 1));                // [4][2][Mp]
-    int8_t* sgall = (int8_t*)(CSall + 8 * Mp);                       // [4][N]
-    int16_t* lstall = (int16_t*)(sgall + 4 * ((N + 1) & ~1));       // [4][Nb]
-    for (int e = threadIdx.x; e < Nb; e += blockDim.x) bonds[e] = bonds_g[e];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int w = blockIdx.x * 4 + wid;
-    cpx<R>* C = CSall + 2 * wid * Mp;
-    cpx<R>* S = C + Mp;
-    int8_t* sg = sgall + wid * ((N + 1) & ~1);
-    int16_t* lst = lstall + wid * Nb;
-    double xsum = 0.0;
-    cpx<double> as = {0.0, 0.0};
-    if (w < nc) {
-        for (int i = lane; i < N; i += 32) {
-            sg[i] = sp[(size_t)w * N + i];
-            as = as + (double)sg[i] * ccast<double>(a_vis[i]);
-        }
-        for (int m = lane; m < M; m += 32) {
-            const cpx<R> th = theta[(size_t)w * M + m];
-            const R ax = th.x < R(0) ? -th.x : th.x;
-            const R e = m_exp(R(-2) * ax), sgn = th.x < R(0) ? R(-1) : R(1);
-            R sn, cs;
-            m_sincos(th.y, &sn, &cs);
-            const R hp = R(0.5) * (R(1) + e), hm = sgn * R(0.5) * (R(1) - e);
-            C[m] = {hp * cs, hm * sn};
-            S[m] = {hm * cs, hp * sn};
-            xsum += (double)ax;
-        }
-    }
+    cpx<R>* thall = (cpx<R>*)(bonds + Nb + (Nb & 1));                // [4][SYM_MC][32]
+    int8_t* sgall = (int8_t*)(thall + 4 * 32 * SYM_MC);              // [128][Nq]
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int wb = blockIdx.x * 128;                                 // first configuration of the block
+    const int w = wb + t;
+    const bool valid = w < nc;
+    for (int e = t; e < Nb; e += 128) bonds[e] = bonds_g[e];
+    const int nblk = nc - wb < 128 ? nc - wb : 128;
+    for (int e = t; e < nblk * N; e += 128) sgall[(e / N) * Nq + e % N] = sp[(size_t)wb * N + e];
     __syncthreads();
-    if (w >= nc) return;
-    xsum = warp_sum(xsum);
-    as = warp_sum(as);
-
+    const int8_t* sg = sgall + t * Nq;
+    cpx<R>* th = thall + wid * 32 * SYM_MC;
+    cpx<double> as = {0.0, 0.0};
+    for (int i = 0; i < N; ++i) as = as + (double)sg[i] * ccast<double>(a_vis[i]);
     R ed = R(0);
-    int n_anti = 0;
-    for (int b0 = 0; b0 < Nb; b0 += 32) {
-        const int b = b0 + lane;
-        bool anti = false;
-        if (b < Nb) {
-            const int2 bd = bonds[b];
-            const int p = sg[bd.x] * sg[bd.y];
-            ed += R(p);
-            anti = p < 0;
-        }
-        const unsigned msk = __ballot_sync(0xffffffffu, anti);
-        if (anti) lst[n_anti + __popc(msk & ((1u << lane) - 1u))] = (int16_t)b;
-        n_anti += __popc(msk);
-    }
-    __syncwarp();
-    const double edd = 0.25 * J * (double)warp_sum(ed);
+    for (int b = 0; b < Nb; ++b) ed += R(sg[bonds[b].x] * sg[bonds[b].y]);
+    double xsum = 0.0;
     cpx<double> off = {0.0, 0.0};
-    for (int k = lane; k < n_anti; k += 32) {
-        const int b = lst[k];
-        const int si = sg[bonds[b].x];
-        const R s = R(si);
-        cpx<R> pr = ea[2 * b + (si > 0 ? 0 : 1)];
-        int ex = 0;
-        for (int m = 0; m < M; ++m) {
-            const cpx<R> ch = ChT[(size_t)m * Nb + b], sh = ShT[(size_t)m * Nb + b];
-            const cpx<R> u = C[m] * ch, v = S[m] * sh;
-            pr = pr * cpx<R>{u.x - s * v.x, u.y - s * v.y};
-            if ((m & 15) == 15) {
-                int e;
-                frexp(fmax(fabs(pr.x), fabs(pr.y)), &e);
-                pr = {ldexp(pr.x, -e), ldexp(pr.y, -e)};
-                ex += e;
+    for (int g0 = 0; g0 < Nb; g0 += GB) {
+        // the pass's bonds: spin of the first site (sign bits) and antiparallel bits
+        // the pass reads table columns base .. base + GB - 1 at constant offsets:
+        // the last pass is moved back to end at Nb, and its columns that the
+        // previous pass took (below g0) are left out of the sum
+        const bool fits = Nb >= GB;
+        const int base = fits ? (g0 + GB <= Nb ? g0 : Nb - GB) : 0;
+        uint32_t anti = 0u;
+        cpx<R> pr[GB];
+        R sv[GB];
+        int ex = 0;  // one power-of-two scale for the pass's products
+#pragma unroll
+        for (int q = 0; q < GB; ++q) {
+            const int b = base + q < Nb ? base + q : Nb - 1;
+            const int sx = sg[bonds[b].x], sy = sg[bonds[b].y];
+            sv[q] = R(sx);
+            if (base + q >= g0 && base + q < Nb && sx != sy) anti |= 1u << q;
+            pr[q] = ea[2 * b + (sx > 0 ? 0 : 1)];
+        }
+        for (int mc = 0; mc < M; mc += SYM_MC) {
+            __syncwarp();
+            for (int e = lane; e < 32 * SYM_MC; e += 32) {
+                const int mm = e >> 5, cf = e & 31, wc = wb + 32 * wid + cf;  // th[mm][cf]
+                th[e] = (wc < nc && mc + mm < M) ? theta[(size_t)wc * M + mc + mm]
+                                                 : cpx<R>{R(0), R(0)};
+            }
+            __syncwarp();
+            const int mlim = M - mc < SYM_MC ? M - mc : SYM_MC;
+            for (int mm = 0; mm < mlim; ++mm) {
+                const int m = mc + mm;
+                const cpx<R> tv = th[mm * 32 + lane];
+                const R ax = tv.x < R(0) ? -tv.x : tv.x;
+                const R e = m_exp(R(-2) * ax), sgn = tv.x < R(0) ? R(-1) : R(1);
+                R sn, cs;
+                m_sincos(tv.y, &sn, &cs);
+                const R hp = R(0.5) * (R(1) + e), hm = sgn * R(0.5) * (R(1) - e);
+                const cpx<R> Cm = {hp * cs, hm * sn}, Sm = {hm * cs, hp * sn};
+                if (g0 == 0) xsum += (double)ax;
+                const cpx<R>* chr = ChT + (size_t)m * Nb + base;
+                const cpx<R>* shr = ShT + (size_t)m * Nb + base;
+                if (fits) {
+#pragma unroll
+                    for (int q = 0; q < GB; ++q) {
+                        const cpx<R> ch = ldg(chr + q), sh = ldg(shr + q);  // same address in every lane
+                        const cpx<R> x = Cm * ch, y = Sm * sh;
+                        pr[q] = pr[q] * cpx<R>{x.x - sv[q] * y.x, x.y - sv[q] * y.y};
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < GB; ++q) {
+                        const int qq = q < Nb ? q : Nb - 1;
+                        const cpx<R> ch = ldg(chr + qq), sh = ldg(shr + qq);
+                        const cpx<R> x = Cm * ch, y = Sm * sh;
+                        pr[q] = pr[q] * cpx<R>{x.x - sv[q] * y.x, x.y - sv[q] * y.y};
+                    }
+                }
+                if ((m & 15) == 15) {
+                    // rescale by the largest: a product 2^-126 below it is
+                    // negligible in the sum
+                    R mx = R(0);
+#pragma unroll
+                    for (int q = 0; q < GB; ++q) mx = fmax(mx, fmax(fabs(pr[q].x), fabs(pr[q].y)));
+                    int ee;
+                    frexp(mx, &ee);
+                    const R sc = ldexp(R(1), -ee);
+#pragma unroll
+                    for (int q = 0; q < GB; ++q) pr[q] = sc * pr[q];
+                    ex += ee;
+                }
             }
         }
-        off = off + cpx<double>{ldexp((double)pr.x, ex), ldexp((double)pr.y, ex)};
+#pragma unroll
+        for (int q = 0; q < GB; ++q)
+            if ((anti >> q) & 1u)
+                off = off + cpx<double>{ldexp((double)pr[q].x, ex), ldexp((double)pr[q].y, ex)};
     }
-    off = warp_sum(off);
-    if (lane == 0) {
+    if (valid) {
         const int s = w % B;
+        const double edd = 0.25 * J * (double)ed;
         const cpx<double> ref = ccast<double>(lp_ref[s]);
         const cpx<double> lam = {as.x + M * 0.69314718055994530942 + xsum - ref.x, as.y - ref.y};
         const cpx<double> v = cexp_(ccast<double>(lp[w]) - ref);
@@ -175,6 +215,7 @@ __global__ void __launch_bounds__(128) sym_hprime_kernel(
         hb[w] = ccast<R>(r);
     }
 }
+
 
 // Bt[(k Nm + n) B + s] = L^-1 sum_m e^{-i 2 pi (k1 m1 + k2 m2) / L} A[m][s]
 template <typename R>
@@ -224,6 +265,26 @@ sym_ws ws_layout(const cr_ctx* c, int B, bool with_h) {
     return o;
 }
 
+// shared memory of sym_hprime_kernel
+template <typename R> size_t sym_hprime_smem(const cr_ctx* c) {
+    return (size_t)(c->Nb + (c->Nb & 1)) * sizeof(int2) + (size_t)4 * 32 * SYM_MC * sizeof(cpx<R>) +
+           (size_t)128 * ((c->N + 3) & ~3);
+}
+
+// Opt sym_hprime_kernel into the shared memory of this context where it
+// exceeds the default (called once per context, outside any capture).
+cr_status sym_prepare_impl(cr_ctx* c) {
+    const size_t s4 = sym_hprime_smem<float>(c), s8 = sym_hprime_smem<double>(c);
+    cudaError_t e = cudaSuccess;
+    if (s4 > 48 * 1024)
+        e = cudaFuncSetAttribute(sym_hprime_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s4);
+    if (e == cudaSuccess && s8 > 48 * 1024)
+        e = cudaFuncSetAttribute(sym_hprime_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s8);
+    return e == cudaSuccess ? CR_OK : cr_fail(c, CR_ECUDA, "sym_prepare: %s", cudaGetErrorString(e));
+}
+
 template <typename R>
 cr_status launch_sym_hprime(cr_ctx* c, const void* params, const int8_t* sp, int nc, int B,
                             const cpx<R>* th, const cpx<R>* lp, const void* lp_ref,
@@ -231,10 +292,9 @@ cr_status launch_sym_hprime(cr_ctx* c, const void* params, const int8_t* sp, int
     cr_status s = build_tables(c, params, 1);
     if (s != CR_OK) return s;
     const cr_tables& t = c->tab[1];
-    const size_t sm = (c->Nb + (c->Nb & 1)) * sizeof(int2) + 8 * (size_t)c->Mp * sizeof(cpx<R>) +
-                      4 * ((c->N + 1) & ~1) + 4 * c->Nb * sizeof(int16_t);
+    const size_t sm = sym_hprime_smem<R>(c);
     CR_LAUNCH(c, CR_KERNEL_TARGET,
-              sym_hprime_kernel<R><<<(unsigned)((nc + 3) / 4), 128, sm, c->stream>>>(
+              sym_hprime_kernel<R><<<(unsigned)((nc + 127) / 128), 128, sm, c->stream>>>(
                   sp, th, lp, (const cpx<R>*)lp_ref, (const cpx<R>*)params, (const cpx<R>*)t.ChT,
                   (const cpx<R>*)t.ShT, (const cpx<R>*)t.ea, c->d_bonds, nc, B, c->N, c->M, c->Mp,
                   c->Nb, c->J, hp[0], hp[1], hp[2], hb));
@@ -299,6 +359,8 @@ cr_status btilde_checked(cr_ctx* ctx, const char* name, const cr_state* states, 
 }
 
 }  // namespace
+
+cr_status sym_prepare(cr_ctx* c) { return sym_prepare_impl(c); }
 
 extern "C" size_t sym_workspace_bytes(const cr_ctx* ctx, int B) {
     if (!ctx || B < 1) return 0;
