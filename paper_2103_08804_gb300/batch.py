@@ -301,7 +301,8 @@ def momentum_scan_specs(L=8, alpha=2, chains=(48, 96), walkers=8192, n_moments=1
                         sigma=0.02, seed=0, **cfg_kw):
     """Every irreducible momentum of an L x L lattice plus chains of the given
     lengths at q = pi/2, alpha = M/N hidden units per site, random RBMs and
-    walkers from synth; rescaling from the rigorous spectrum bounds."""
+    walkers from synth; rescaling from the rigorous spectrum bounds; the
+    shift from synth.default_shift unless given."""
     from . import synth
     lat = [((L, L), q) for q in square_irreducible_momenta(L)]
     lat += [((n, 1), (np.pi / 2, 0.0)) for n in chains]
@@ -309,8 +310,10 @@ def momentum_scan_specs(L=8, alpha=2, chains=(48, 96), walkers=8192, n_moments=1
     for k, ((Lx, Ly), q) in enumerate(lat):
         N, M = Lx * Ly, alpha * Lx * Ly
         E0, a = synth.safe_rescaling(Lx, Ly)
+        kw = dict(cfg_kw)
+        kw.setdefault("shift", synth.default_shift(N + M + N * M, walkers))
         cfg = SeqConfig(Lx=Lx, Ly=Ly, M=M, q=q, n_moments=n_moments, n_iter=n_iter, E0=E0, a=a,
-                        seed=2 * k, seed_ref=2 * k + 1, **cfg_kw)
+                        seed=2 * k, seed_ref=2 * k + 1, **kw)
         name = f"square{L}_q{q[0]:.4f}_{q[1]:.4f}" if Ly > 1 else f"chain{Lx}_q{q[0]:.4f}"
         specs.append(SeqSpec(name, cfg, synth.rbm_params(seed + 100 + k, N, M, sigma),
                              synth.sz0_spins(seed + 200 + k, walkers, N),

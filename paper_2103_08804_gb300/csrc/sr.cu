@@ -769,8 +769,11 @@ static cr_status sr_step_t(cr_ctx* c, void* params, const int8_t* spins, const v
     double* redR = c->red;
     double* redO = c->red + 2 * (P + 2 + c->M);
     cr_status s;
-    if (c->ored && !o->cg_precond) {
-        // mixed: both estimator sums in one tensor-core launch
+    if (c->ored && o->solver == CR_SOLVE_CG && !o->cg_precond) {
+        // mixed, matrix-free CG: both estimator sums in one tensor-core launch
+        // (about 3e-7 of the summed terms).  The direct solve of an explicit S
+        // keeps the compensated float32 sums (about 1e-8): it solves at the
+        // small shift exactly, with no CG budget to damp their error.
         s = launch_oreduce_tc(c, spins, T, Rv, B, redR, redO);
     } else {
         s = oreduce(c, true, spins, T, Rv, B, redR, nullptr);
