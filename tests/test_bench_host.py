@@ -85,3 +85,22 @@ def test_cg_summary_counts_truncated_solves():
     # at the limit and above tolerance: (0,0) and (1,0); (0,2) met the tolerance
     assert abs(s["cg_truncated_fraction"] - 2 / 6) < 1e-12
     assert s["cg_rel_residual_max"] == 3e-3
+
+
+def test_shift_rule_of_the_workloads():
+    # 0.1 where the parameters reach the walker count (S singular), 1e-3
+    # otherwise; the batch specs take it per sequence unless a shift is given
+    from paper_2103_08804_gb300 import batch, synth
+    assert synth.default_shift(8384, 8192) == 0.1
+    assert synth.default_shift(8384, 16384) == 1e-3
+    assert synth.WORKLOADS["square16"].shift == 0.1
+    assert synth.WORKLOADS["square10"].shift == 1e-2
+    assert synth.WORKLOADS["chain64"].shift == 1e-3
+    specs = batch.momentum_scan_specs(L=8, alpha=2, chains=(48, 96), walkers=8192, n_moments=2,
+                                      n_iter=1)
+    shifts = {s.name: s.cfg.shift for s in specs}
+    assert all(v == 0.1 for k, v in shifts.items() if k.startswith("square8"))
+    assert shifts["chain48_q1.5708"] == 1e-3 and shifts["chain96_q1.5708"] == 0.1
+    given = batch.momentum_scan_specs(L=4, alpha=2, chains=(), walkers=64, n_moments=2, n_iter=1,
+                                      shift=0.5)
+    assert all(s.cfg.shift == 0.5 for s in given)

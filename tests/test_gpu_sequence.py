@@ -204,8 +204,8 @@ def _single_steps(seq, ref, e0, solver):
 #   Cholesky: rounding only, agreement to 1e-9;
 #   CG: two solves stopping at |r| <= 1e-10 |F| may differ by kappa 1e-10.
 # float32 and mixed paths, against the oracle's direct solve: the moments are
-# held to the parity bar of the benchmark spec, 1e-5 mu_0 (float32) and 1e-3 mu_0
-# (mixed), with the walker sums of F and <O> compensated (float32 chunk sums
+# held to the parity bar of the method's precision modes, 1e-5 mu_0 (float32)
+# and 1e-3 mu_0 (mixed), with the walker sums of F and <O> compensated (float32 chunk sums
 # left ~1e-5); the float32 CG runs to 1e-7.  beta_n and the parameters are
 # not invariant under the near-null directions of S + lambda I (a scale of
 # t~_n moves beta_n against it, kappa amplifies both).  The state itself,
