@@ -1072,11 +1072,16 @@ def run_explicit(args):
     # and the whole natural-gradient update (S, factor, refined solve)
     if args.eager:
         raise SystemExit("--workload square10 times its kernels on the graph-mode buffers")
+    # (on a restarted sequence: a few more iterations of moment 2, whose fit is
+    # settled, rather than of the last timed moment, whose later iterations
+    # can turn non-finite on these random RBMs)
+    restart(seq)
+    torch.cuda.synchronize()
     ctx.time_kernel("sbuild", 64)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     n_eager = 2
-    kind = seq.kind_of(cycle_moment(K - 1))  # the graph buffers hold the last fitted moment
+    kind = seq.kind_of(CYCLE[0] - 1)  # the graph buffers hold the last fitted moment
     for _ in range(n_eager):
         seq._iteration(kind)
     e1.record(stream)
