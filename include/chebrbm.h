@@ -344,7 +344,11 @@ cr_status cheb_init_params(cr_ctx* ctx, int n, const void* psi, const void* prev
    tanh_theta [B][M] at the samples; R complex [B]; stats_out float64
    [CR_STATS_LEN] (device) or NULL.  shift >= 0 (shift 0 needs S itself
    positive definite: a rank-deficient S then gives CR_ESINGULAR on the
-   Cholesky path). */
+   Cholesky path).  Walker sums of the estimators: float64 in CR_FP64;
+   compensated float32 chunk sums combined in float64 in CR_FP32, and in
+   CR_MIXED for Cholesky and Jacobi-preconditioned solves; in CR_MIXED with
+   plain CG both sums are one tensor-core launch (three-term bf16 splits,
+   float32 accumulation over K segments, float64 across them). */
 cr_status sr_step(cr_ctx* ctx, void* params, const int8_t* spins, const void* tanh_theta,
                   const void* R, int B, const cr_sr_opts* opts, double* stats_out);
 
