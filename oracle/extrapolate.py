@@ -62,6 +62,11 @@ def lp_roots(a):
     return np.linalg.eigvals(C)
 
 
+def stabilise(z):
+    """Step 3: roots outside the unit circle are moved onto it."""
+    return np.where(np.abs(z) > 1.0, z / np.abs(z), z)
+
+
 def extrapolate(mu, p, n0, n_out, reg=1e-12):
     """The first n_out moments: the known ones, then the prediction.
 
@@ -74,7 +79,7 @@ def extrapolate(mu, p, n0, n_out, reg=1e-12):
     z = lp_roots(a)
     V = np.power.outer(z, np.arange(p)).T          # V[m, k] = z_k^m
     c = np.linalg.solve(V, mu[N - p:])
-    w = np.where(np.abs(z) > 1.0, z / np.abs(z), z)
+    w = stabilise(z)
     out = np.empty(n_out, dtype=np.complex128)
     out[:N] = mu
     m = np.arange(p, n_out - N + p)                 # mu_{N-p+m}, m >= p

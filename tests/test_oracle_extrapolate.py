@@ -83,8 +83,75 @@ def test_exact_chain_moments_are_predicted():
     assert np.max(np.abs(out - mu)) < 1e-5 * abs(mu[0])
 
 
+def test_coefficients_are_the_least_squares_solution():
+    """Without the Tikhonov term the coefficients minimise the one-step
+    prediction error over the window: on arbitrary complex data they equal
+    the library least-squares solution (SVD) of the data matrix."""
+    g = np.random.Generator(np.random.Philox(17))
+    mu = g.standard_normal(40) + 1j * g.standard_normal(40)
+    p, n0 = 5, 10
+    A = np.array([mu[n - p:n][::-1] for n in range(n0, 40)])
+    want = np.linalg.lstsq(A, -mu[n0:40], rcond=None)[0]
+    assert np.max(np.abs(ex.lp_coefficients(mu, p, n0, 0.0) - want)) < 1e-10
+
+
 def test_bad_arguments():
     mu = cosines()[:50]
     for p, n0, n_out in ((0, 10, 60), (20, 10, 60), (10, 50, 60), (10, 20, 40)):
         with pytest.raises(ValueError):
             ex.extrapolate(mu, p, n0, n_out)
+
+
+def _pins_fail():
+    """True when at least one pin above fails."""
+    checks = (test_sum_of_cosines_is_continued_exactly, test_damped_exponentials_and_their_roots,
+              test_single_cosine_roots_on_the_unit_circle, test_growing_mode_is_put_on_the_unit_circle,
+              test_exact_chain_moments_are_predicted,
+              test_coefficients_are_the_least_squares_solution)
+    for f in checks:
+        try:
+            f()
+        except (AssertionError, np.linalg.LinAlgError, ValueError):
+            return True
+    return False
+
+
+def test_planted_mistakes_fail_a_pin(monkeypatch):
+    """Plausible mistakes planted in the oracle (on the CPU) each fail a pin:
+    the normal equations without the conjugate, a lag off by one, the sign
+    of the prediction coefficients, growing roots left in place."""
+    good_ne, good_coef, good_roots = ex.normal_equations, ex.lp_coefficients, ex.lp_roots
+    assert not _pins_fail()
+
+    def no_conj(mu, p, n0, reg):
+        mu = np.asarray(mu, dtype=np.complex128)
+        R = np.zeros((p, p), dtype=np.complex128)
+        r = np.zeros(p, dtype=np.complex128)
+        for n in range(n0, len(mu)):
+            past = mu[n - p:n][::-1]
+            R += np.outer(past, past)
+            r += past * mu[n]
+        return R + reg * np.max(np.abs(np.diag(R))) * np.eye(p), r
+
+    def lag_off(mu, p, n0, reg):
+        mu = np.asarray(mu, dtype=np.complex128)
+        R = np.zeros((p, p), dtype=np.complex128)
+        r = np.zeros(p, dtype=np.complex128)
+        for n in range(max(n0, p + 1), len(mu)):
+            past = mu[n - p - 1:n - 1][::-1]
+            R += np.outer(np.conj(past), past)
+            r += np.conj(past) * mu[n]
+        return R + reg * np.max(np.real(np.diag(R))) * np.eye(p), r
+
+    for name, fn in (("normal_equations", no_conj), ("normal_equations", lag_off),
+                     ("lp_coefficients", lambda *a: -good_coef(*a))):
+        monkeypatch.setattr(ex, name, fn)
+        assert _pins_fail(), name
+        monkeypatch.setattr(ex, "normal_equations", good_ne)
+        monkeypatch.setattr(ex, "lp_coefficients", good_coef)
+    # growing roots kept: the clipped-mode pin must fail
+    monkeypatch.setattr(ex, "stabilise", lambda z: z)
+    with pytest.raises(AssertionError):
+        test_growing_mode_is_put_on_the_unit_circle()
+    monkeypatch.undo()
+    assert good_roots is ex.lp_roots
