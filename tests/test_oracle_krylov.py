@@ -73,3 +73,22 @@ def test_poles_are_gauss_quadrature_and_lanczos_ritz_values():
             V.append(w_ / beta[-1])
     Tm = np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1)
     assert np.allclose(np.sort(lam), np.linalg.eigvalsh(Tm), atol=1e-9)
+
+
+def test_sampled_H_is_hermitian():
+    """On sampled columns (plain means over a subset of the configurations)
+    the raw estimator <conj(B_n) HB_m> is not Hermitian; the projected H
+    the Krylov step uses is (its sampled form is Hermitised), with a real
+    diagonal, and G is Hermitian positive semi-definite."""
+    Hp, t0, psi, _, _, _ = _setup(6)
+    ts = exact.chebyshev_vectors(Hp, t0, 6)
+    g = np.random.default_rng(4)
+    idx = g.choice(len(psi), size=60, replace=True)
+    B = [(t / psi)[idx] for t in ts]
+    HB = [((Hp @ t) / psi)[idx] for t in ts]
+    raw = (np.conj(np.array(B)) / 60) @ np.array(HB).T
+    assert np.max(np.abs(raw - raw.conj().T)) > 1e-6
+    G, Hm = krylov.gram(B, HB)
+    assert np.array_equal(Hm, Hm.conj().T)
+    assert np.max(np.abs(G - G.conj().T)) <= 1e-14 * np.max(np.abs(G))
+    assert np.min(np.linalg.eigvalsh(0.5 * (G + G.conj().T))) > -1e-12 * np.max(np.abs(G))
